@@ -1,0 +1,212 @@
+/*
+ * turbofft.h -- C ABI of a batched 1-D complex-to-complex FFT for NVIDIA
+ * GB300 (sm_103a) with online two-sided algorithm-based fault tolerance.
+ *
+ * Method: TurboFFT (PPoPP'25).
+ *   - Transform: the DFT of Sec. 2.2.1,
+ *       forward  y_j = sum_n x_n exp(-2 pi i j n / N)
+ *       inverse  x_j = (1/N) sum_n y_n exp(+2 pi i j n / N)
+ *     computed as a Stockham FFT (Sec. 3.2), in one pass over HBM for
+ *     N <= 2^14 (float32) / 2^13 (float64) and in two passes (four-step,
+ *     N = N1 * N2, the kernel-level tiling of Sec. 3.1) up to N = 2^24.
+ *   - Fault tolerance: the two-sided checksum of Sec. 4.1 (Eq. 4-5) fused
+ *     into the transform kernels (Sec. 4.2.2), amortised over several
+ *     transactions of one thread block (Sec. 4.3), with the location
+ *     encoding (1, 2, ...) of Sec. 4.1 and the delayed, batched correction
+ *     of Sec. 4.1.2.  The fault model is one soft error per checksum group
+ *     (Sec. 2.2.4).
+ *
+ * Conventions for every entry point
+ *   - No call allocates or frees caller memory.  A plan owns every device
+ *     and pinned-host buffer it allocates (tables, the intermediate buffer of
+ *     two-pass plans, the fault-tolerance report and correction records) and
+ *     frees them in turbofft_destroy.
+ *   - Data layout: `batch` transforms of `n` interleaved complex values
+ *     (re, im), contiguous, transform b at element offset b * n.  Element
+ *     type is float (TURBOFFT_C2C_F32, 8 bytes per value) or double
+ *     (TURBOFFT_C2C_F64, 16 bytes per value).
+ *   - Device pointers must be 16-byte aligned device memory on the plan's
+ *     device.  Out-of-place only: `in` is never written.
+ *   - Status codes: every function returns TURBOFFT_SUCCESS or an error;
+ *     no function aborts the process.  Launch-time CUDA errors are reported
+ *     as TURBOFFT_CUDA_ERROR with the CUDA message in turbofft_last_error.
+ *   - A plan is not thread-safe: calls on one plan must not overlap from
+ *     several host threads.  Distinct plans are independent.
+ */
+#ifndef TURBOFFT_H
+#define TURBOFFT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* cudaStream_t is `struct CUstream_st *`; NULL is the legacy default stream. */
+struct CUstream_st;
+typedef struct CUstream_st *turbofft_stream;
+
+typedef enum {
+  TURBOFFT_SUCCESS = 0,
+  TURBOFFT_INVALID_VALUE = 1,     /* bad size, pointer, alignment or enum */
+  TURBOFFT_UNSUPPORTED = 2,       /* valid request this library does not do (in-place) */
+  TURBOFFT_ALLOC_FAILED = 3,      /* device or pinned allocation failed */
+  TURBOFFT_CUDA_ERROR = 4,        /* a CUDA runtime call failed */
+  TURBOFFT_FT_UNCORRECTABLE = 5,  /* the last exec saw an error it could not fix */
+  TURBOFFT_TIMEOUT = 6            /* reserved: a bounded device wait expired */
+} turbofft_status;
+
+typedef enum {
+  TURBOFFT_C2C_F32 = 0,           /* complex64: float re, float im */
+  TURBOFFT_C2C_F64 = 1            /* complex128: double re, double im */
+} turbofft_dtype;
+
+/* direction argument of turbofft_plan_create */
+#define TURBOFFT_FORWARD (-1)          /* y = W x,            W = (w^{jk}), w = e^{-2 pi i/N} */
+#define TURBOFFT_INVERSE (1)           /* y = (1/N) conj(W) x  (Sec. 2.2.1 inverse) */
+#define TURBOFFT_INVERSE_UNSCALED (2)  /* y = conj(W) x = W^H x, the adjoint of FORWARD */
+
+typedef enum {
+  TURBOFFT_FT_OFF = 0,            /* plain FFT, no checksums */
+  TURBOFFT_FT_DETECT = 1,         /* checksums fused; detect and locate, report only */
+  TURBOFFT_FT_CORRECT = 2         /* detect, locate and correct in place (Sec. 4.1.2) */
+} turbofft_ft_mode;
+
+typedef struct turbofft_plan turbofft_plan;
+
+/*
+ * A fault-injection site (Sec. 5.3.1 flips one bit of one value of one
+ * signal).  Coordinates are the plan's own:
+ *   transform  index of the transform in the batch, [0, batch)
+ *   pass       kernel pass, [0, info.num_passes)
+ *   stage      radix stage of that pass, [0, info.stages[pass]]: the value
+ *              entering radix stage `stage` (0 = as loaded, after the input
+ *              checksum is taken); stage == info.stages[pass] is the pass's
+ *              output before its output checksum is taken
+ *   element    [0, n): index of the value in the transform's working array
+ *              at that stage.  For a two-pass plan with n = N1 * N2 the
+ *              working array of pass 0 holds column n2 at elements
+ *              p * N2 + n2 (p = position within the length-N1 column) and
+ *              that of pass 1 holds row k1 at elements k1 * N2 + p.
+ *   component  0 = real part, 1 = imaginary part
+ */
+typedef struct {
+  int64_t transform;
+  int32_t pass;
+  int32_t stage;
+  int64_t element;
+  int32_t component;
+} turbofft_site;
+
+/* Outcome of the most recent turbofft_exec on a plan with ft_mode != OFF. */
+typedef struct {
+  int64_t groups_checked;   /* checksum groups verified (all passes) */
+  int64_t detected;         /* groups whose checksum test failed */
+  int64_t located;          /* of those, groups where one signal was identified */
+  int64_t corrected;        /* signals corrected (CORRECT mode) */
+  int64_t recomputed;       /* of the corrected, fixed by recomputing from the input */
+  int64_t uncorrectable;    /* detected groups that could not be fixed / located */
+  int64_t first_transform;  /* transform of the first located error, -1 if none */
+  int32_t first_pass;       /* pass of the first detection, -1 if none */
+  int32_t reserved;
+  double first_residual;    /* |S1| of the first detected group */
+  double first_threshold;   /* tau of that group */
+  double max_clean_ratio;   /* max |S1| / tau over groups that passed */
+} turbofft_report;
+
+/* Static facts about a plan. */
+typedef struct {
+  int64_t n, batch;
+  int32_t dtype, direction, ft_mode;
+  int32_t num_passes;       /* 1 or 2 */
+  int64_t sub_n[2];         /* sub-transform length of each pass (n = sub_n[0] * sub_n[1]) */
+  int32_t stages[2];        /* radix stages of each pass */
+  int32_t radix[2];         /* radix of the register-level butterflies of each pass */
+  int32_t group_transactions; /* transactions of one thread block per checksum group */
+  int32_t grid[2];          /* persistent thread blocks launched per pass */
+  int32_t block[2];         /* threads per block per pass */
+  int64_t workspace_bytes;  /* device memory the plan owns */
+} turbofft_plan_info;
+
+/*
+ * Create a plan on the current CUDA device.
+ *   n          transform length, a power of two in [8, 2^24]
+ *   batch      number of transforms, >= 1, batch * n <= 2^31 elements
+ *   dtype      TURBOFFT_C2C_F32 or TURBOFFT_C2C_F64
+ *   direction  TURBOFFT_FORWARD, TURBOFFT_INVERSE or TURBOFFT_INVERSE_UNSCALED
+ *   ft_mode    TURBOFFT_FT_OFF / _DETECT / _CORRECT
+ *   plan       out: the new plan (set to NULL on failure)
+ * Tables (twiddles, checksum vectors e and e^T W) are computed on the host
+ * in long double / double and copied to the device here, synchronously.
+ * Errors: INVALID_VALUE for any argument out of range, ALLOC_FAILED,
+ * CUDA_ERROR (no device, or a copy failed).
+ */
+turbofft_status turbofft_plan_create(int64_t n, int64_t batch, turbofft_dtype dtype,
+                                     int direction, turbofft_ft_mode ft_mode,
+                                     turbofft_plan **plan);
+
+/*
+ * Transform `in` into `out` (both device pointers, see the layout above) on
+ * `stream`.  Asynchronous: returns after queueing the kernels.  in == out
+ * (or overlapping buffers) returns TURBOFFT_UNSUPPORTED.  With ft_mode !=
+ * OFF the checksums are verified on the device and the outcome is read with
+ * turbofft_get_report.  A site armed with turbofft_inject is applied to this
+ * exec and then disarmed.
+ * Errors: INVALID_VALUE (NULL or misaligned pointer), UNSUPPORTED,
+ * CUDA_ERROR (launch failed).
+ */
+turbofft_status turbofft_exec(turbofft_plan *plan, const void *in, void *out,
+                              turbofft_stream stream);
+
+/*
+ * Same transform with HOST buffers: copies `host_in` to the device, runs
+ * the transform and copies the result to `host_out`, pipelined in chunks of
+ * the batch over two internal streams ordered after `stream`, and returns
+ * when `host_out` is complete.  Host buffers should be pinned
+ * (cudaHostAlloc / cudaHostRegister) for full bandwidth; pageable memory
+ * works but is slower.  The plan allocates its device staging buffers on
+ * the first call and keeps them until destroy.
+ */
+turbofft_status turbofft_exec_host(turbofft_plan *plan, const void *host_in, void *host_out,
+                                   turbofft_stream stream);
+
+/*
+ * Arm a one-shot fault for the next exec: flip bit `bit` of the value at
+ * `site` (coordinates above).  bit in [0, 31] (F32) or [0, 63] (F64).
+ * Errors: INVALID_VALUE for any coordinate out of range.
+ */
+turbofft_status turbofft_inject(turbofft_plan *plan, turbofft_site site, int bit);
+
+/*
+ * Wait for the most recent exec on this plan and read its fault-tolerance
+ * report.  Returns TURBOFFT_FT_UNCORRECTABLE (with *report filled) if that
+ * exec left an error it could not correct (or, in DETECT mode, detected
+ * one); SUCCESS otherwise.  With ft_mode == OFF the report is all zero.
+ */
+turbofft_status turbofft_get_report(turbofft_plan *plan, turbofft_report *report);
+
+/* Fill *info with the plan's static facts. */
+turbofft_status turbofft_plan_get_info(const turbofft_plan *plan, turbofft_plan_info *info);
+
+/*
+ * Scale the detection threshold tau by `factor` (> 0; 1 restores the
+ * default).  For threshold studies (detection vs false-alarm rate,
+ * Sec. 5.3.1); the default is calibrated for zero false alarms.
+ */
+turbofft_status turbofft_set_threshold_scale(turbofft_plan *plan, double factor);
+
+/* Free everything the plan owns.  NULL is a no-op.  Waits for the plan's
+ * outstanding work first. */
+turbofft_status turbofft_destroy(turbofft_plan *plan);
+
+/* Static, human-readable name of a status code. */
+const char *turbofft_status_string(turbofft_status status);
+
+/* Text of the last CUDA error seen by this plan ("" if none). */
+const char *turbofft_last_error(const turbofft_plan *plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TURBOFFT_H */

@@ -32,8 +32,10 @@ Readings where the paper is silent (each listed in the design doc):
   * correction re-checks the corrected signal; if the paper's Delta
     correction does not pass (e.g. Delta is not finite), the signal is
     recomputed from its untouched input; if that fails too, the group is
-    reported uncorrectable.  More than one corrupted signal in a group
-    violates the single-event model and is reported uncorrectable.
+    reported uncorrectable.  After a correction every other signal of the
+    group is re-verified on its own checksum: more than one corrupted signal
+    in a group violates the single-event model and is reported
+    uncorrectable.
 """
 from __future__ import annotations
 
@@ -201,12 +203,10 @@ def correct_group(x, y, e, v, precision, gamma: float = GAMMA_DEFAULT,
         return math.isfinite(rr.real) and math.isfinite(rr.imag) and _mag(rr) <= tb
 
     def group_passes(yy):
-        # after the fix the whole group must pass again: a second corrupted
-        # signal (outside the single-event model) would still show here
-        s_in, s_out = checksums(x, yy, e, v)
-        with np.errstate(all="ignore"):
-            S1 = complex(np.sum(s_out - s_in))
-        return math.isfinite(S1.real) and math.isfinite(S1.imag) and _mag(S1) <= rep["tau"]
+        # after the fix every other signal of the group must pass its own
+        # checksum test: a second corrupted signal (outside the single-event
+        # model) would still show here
+        return all(passes(yy[b], x[b]) for b in range(G) if b != k)
 
     # paper's correction: Delta = y_bar - W x_bar, y_k <- y_k - Delta
     with np.errstate(all="ignore"):

@@ -1,0 +1,226 @@
+"""Python binding of libturbofft (include/turbofft.h): argument marshalling
+only.  Every step of the transform and of the fault tolerance runs in the
+library's CUDA kernels; PyTorch provides device memory and streams.
+
+    import paper_2412_05824_gb300 as tf
+    plan = tf.Plan(n=1024, batch=4096, dtype="complex64", direction="forward", ft="correct")
+    y = plan.exec(x)                      # x: CUDA complex tensor [batch, n]
+    rep = plan.report()                   # fault-tolerance outcome of that exec
+
+There is no fallback: if the compiled library is missing the import of
+`lib()` raises, and so does every call that needs it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libturbofft.so")
+
+# status codes
+SUCCESS = 0
+INVALID_VALUE = 1
+UNSUPPORTED = 2
+ALLOC_FAILED = 3
+CUDA_ERROR = 4
+FT_UNCORRECTABLE = 5
+TIMEOUT = 6
+
+C2C_F32 = 0
+C2C_F64 = 1
+FORWARD = -1
+INVERSE = 1
+INVERSE_UNSCALED = 2
+FT_OFF = 0
+FT_DETECT = 1
+FT_CORRECT = 2
+
+_DIRS = {"forward": FORWARD, "inverse": INVERSE, "inverse_unscaled": INVERSE_UNSCALED,
+         FORWARD: FORWARD, INVERSE: INVERSE, INVERSE_UNSCALED: INVERSE_UNSCALED}
+_FT = {"off": FT_OFF, "detect": FT_DETECT, "correct": FT_CORRECT, None: FT_OFF, False: FT_OFF,
+       FT_OFF: FT_OFF, FT_DETECT: FT_DETECT, FT_CORRECT: FT_CORRECT}
+
+
+class Site(ctypes.Structure):
+    _fields_ = [("transform", ctypes.c_int64), ("pass_", ctypes.c_int32), ("stage", ctypes.c_int32),
+                ("element", ctypes.c_int64), ("component", ctypes.c_int32)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("groups_checked", ctypes.c_int64), ("detected", ctypes.c_int64),
+                ("located", ctypes.c_int64), ("corrected", ctypes.c_int64),
+                ("recomputed", ctypes.c_int64), ("uncorrectable", ctypes.c_int64),
+                ("first_transform", ctypes.c_int64), ("first_pass", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("first_residual", ctypes.c_double),
+                ("first_threshold", ctypes.c_double), ("max_clean_ratio", ctypes.c_double)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("batch", ctypes.c_int64), ("dtype", ctypes.c_int32),
+                ("direction", ctypes.c_int32), ("ft_mode", ctypes.c_int32),
+                ("num_passes", ctypes.c_int32), ("sub_n", ctypes.c_int64 * 2),
+                ("stages", ctypes.c_int32 * 2), ("radix", ctypes.c_int32 * 2),
+                ("group_transactions", ctypes.c_int32), ("grid", ctypes.c_int32 * 2),
+                ("block", ctypes.c_int32 * 2), ("workspace_bytes", ctypes.c_int64)]
+
+
+EXPORTS = [
+    "turbofft_plan_create", "turbofft_exec", "turbofft_exec_host", "turbofft_inject",
+    "turbofft_get_report", "turbofft_plan_get_info", "turbofft_set_threshold_scale",
+    "turbofft_destroy", "turbofft_status_string", "turbofft_last_error",
+]
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libturbofft.so (built by build.py / __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libturbofft.so is not built (%s); run paper_2412_05824_gb300/build.py" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    L.turbofft_plan_create.argtypes = [i64, i64, i32, i32, i32, ctypes.POINTER(vp)]
+    L.turbofft_exec.argtypes = [vp, vp, vp, vp]
+    L.turbofft_exec_host.argtypes = [vp, vp, vp, vp]
+    L.turbofft_inject.argtypes = [vp, Site, i32]
+    L.turbofft_get_report.argtypes = [vp, ctypes.POINTER(Report)]
+    L.turbofft_plan_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+    L.turbofft_set_threshold_scale.argtypes = [vp, ctypes.c_double]
+    L.turbofft_destroy.argtypes = [vp]
+    L.turbofft_status_string.argtypes = [i32]
+    L.turbofft_status_string.restype = ctypes.c_char_p
+    L.turbofft_last_error.argtypes = [vp]
+    L.turbofft_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("turbofft_status_string", "turbofft_last_error"):
+            getattr(L, name).restype = i32
+    _lib = L
+    return L
+
+
+class TurboFFTError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str = ""):
+        name = lib().turbofft_status_string(status).decode()
+        super().__init__("%s: %s%s" % (what, name, (" (" + detail + ")") if detail else ""))
+        self.status = status
+
+
+def _check(status: int, what: str, plan=None):
+    if status != SUCCESS:
+        detail = lib().turbofft_last_error(plan).decode() if plan else ""
+        raise TurboFFTError(status, what, detail)
+
+
+def _dtype_code(dtype) -> int:
+    import torch
+    if dtype in ("complex64", "c64", "f32", torch.complex64, C2C_F32):
+        return C2C_F32
+    if dtype in ("complex128", "c128", "f64", torch.complex128, C2C_F64):
+        return C2C_F64
+    raise ValueError("dtype must be complex64 or complex128, got %r" % (dtype,))
+
+
+class Plan:
+    """A turbofft plan: batch transforms of length n (owns its device tables)."""
+
+    def __init__(self, n: int, batch: int, dtype="complex64", direction="forward", ft="off"):
+        self.n, self.batch = int(n), int(batch)
+        self.dtype_code = _dtype_code(dtype)
+        self.direction = _DIRS[direction]
+        self.ft_mode = _FT[ft]
+        h = ctypes.c_void_p()
+        _check(lib().turbofft_plan_create(self.n, self.batch, self.dtype_code, self.direction,
+                                          self.ft_mode, ctypes.byref(h)), "turbofft_plan_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def torch_dtype(self):
+        import torch
+        return torch.complex64 if self.dtype_code == C2C_F32 else torch.complex128
+
+    def exec(self, x, out=None, stream=None):
+        """y = transform(x) for a contiguous CUDA tensor x of shape [batch, n]."""
+        import torch
+        if not (x.is_cuda and x.dtype == self.torch_dtype and x.is_contiguous() and x.numel() == self.n * self.batch):
+            raise ValueError("x must be a contiguous CUDA %s tensor with %d elements" % (self.torch_dtype, self.n * self.batch))
+        if out is None:
+            out = torch.empty_like(x)
+        if stream is None:
+            stream = torch.cuda.current_stream(x.device)
+        _check(lib().turbofft_exec(self._h, x.data_ptr(), out.data_ptr(), stream.cuda_stream), "turbofft_exec", self._h)
+        return out
+
+    def exec_ptr(self, in_ptr: int, out_ptr: int, stream_ptr: int = 0) -> int:
+        """Raw call through the C ABI; returns the status code."""
+        return lib().turbofft_exec(self._h, in_ptr, out_ptr, stream_ptr)
+
+    def exec_host(self, x_host, out_host=None, stream=None):
+        """Transform CPU (ideally pinned) tensors: copies in, transforms, copies out."""
+        import torch
+        if x_host.is_cuda or x_host.dtype != self.torch_dtype or not x_host.is_contiguous():
+            raise ValueError("x_host must be a contiguous CPU %s tensor" % self.torch_dtype)
+        if out_host is None:
+            out_host = torch.empty_like(x_host)
+        s = 0 if stream is None else stream.cuda_stream
+        _check(lib().turbofft_exec_host(self._h, x_host.data_ptr(), out_host.data_ptr(), s), "turbofft_exec_host", self._h)
+        return out_host
+
+    def inject(self, transform: int, pass_: int, stage: int, element: int, component: int, bit: int):
+        site = Site(int(transform), int(pass_), int(stage), int(element), int(component))
+        _check(lib().turbofft_inject(self._h, site, int(bit)), "turbofft_inject")
+
+    def report(self) -> dict:
+        r = Report()
+        st = lib().turbofft_get_report(self._h, ctypes.byref(r))
+        if st not in (SUCCESS, FT_UNCORRECTABLE):
+            _check(st, "turbofft_get_report", self._h)
+        d = {name: getattr(r, name) for name, _ in Report._fields_ if name != "reserved"}
+        d["status"] = st
+        return d
+
+    def info(self) -> dict:
+        i = PlanInfo()
+        _check(lib().turbofft_plan_get_info(self._h, ctypes.byref(i)), "turbofft_plan_get_info")
+        d = {}
+        for name, _ in PlanInfo._fields_:
+            v = getattr(i, name)
+            d[name] = list(v) if hasattr(v, "__len__") else v
+        return d
+
+    def set_threshold_scale(self, factor: float):
+        _check(lib().turbofft_set_threshold_scale(self._h, float(factor)), "turbofft_set_threshold_scale")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().turbofft_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_plan_cache: dict = {}
+
+
+def fft(x, inverse: bool = False, scaled: bool = True, ft="off"):
+    """Batched 1-D FFT over the last dimension of a CUDA complex tensor."""
+    n = x.shape[-1]
+    batch = x.numel() // n
+    direction = (INVERSE if scaled else INVERSE_UNSCALED) if inverse else FORWARD
+    key = (n, batch, _dtype_code(x.dtype), direction, _FT[ft], x.device.index)
+    plan = _plan_cache.get(key)
+    if plan is None:
+        plan = _plan_cache[key] = Plan(n, batch, x.dtype, direction, ft)
+    xc = x.contiguous()
+    return plan.exec(xc.view(batch, n)).view(x.shape)

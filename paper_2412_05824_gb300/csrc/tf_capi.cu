@@ -1,0 +1,679 @@
+// Host side of the C ABI declared in include/turbofft.h: plan creation (tables,
+// pass split, launch shapes), exec, injection, report.
+//
+// Tables (TurboFFT Sec. 5.1.2: twiddles precomputed instead of evaluating
+// trigonometric functions on the device; Sec. 4.2.2: the left encoding
+// vector e^T W precomputed outside the transform) are evaluated on the host
+// in long double and rounded once to the plan's precision.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <complex>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/turbofft.h"
+#include "tf_device.cuh"
+#include "tf_registry.h"
+
+using tf::FtRecord;
+using tf::FtState;
+using tf::KernelEntry;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// kernel registry
+// ---------------------------------------------------------------------------
+struct Registry {
+  std::vector<const KernelEntry*> all;
+  Registry() {
+    tf::EntryTableFn fns[] = {tf::entries_f32_sp, tf::entries_f32_col, tf::entries_f32_row,
+                              tf::entries_f64_sp, tf::entries_f64_col, tf::entries_f64_row};
+    for (auto fn : fns) {
+      int n = 0;
+      const KernelEntry* t = fn(&n);
+      for (int i = 0; i < n; ++i) all.push_back(&t[i]);
+    }
+  }
+  const KernelEntry* find(int dtype, int kind, int ns) const {
+    for (auto e : all)
+      if (e->dtype == dtype && e->kind == kind && e->ns == ns) return e;
+    return nullptr;
+  }
+  int max_sp(int dtype) const {
+    int m = 0;
+    for (auto e : all)
+      if (e->dtype == dtype && e->kind == tf::KIND_SP) m = std::max(m, e->ns);
+    return m;
+  }
+};
+const Registry& registry() {
+  static Registry r;
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// host tables (long double)
+// ---------------------------------------------------------------------------
+typedef long double ld;
+typedef std::complex<ld> cld;
+const ld kTwoPi = 6.283185307179586476925286766559005768394338798750L;
+
+// w_n^q = exp(-2 pi i q / n), phase reduced exactly in integers
+cld root(int64_t n, int64_t q) {
+  q %= n;
+  if (q < 0) q += n;
+  ld ang = -kTwoPi * (ld)q / (ld)n;
+  return cld(cosl(ang), sinl(ang));
+}
+
+// forward DFT of a (length power of two), recursive radix-2, long double
+void host_fft(std::vector<cld>& a) {
+  const size_t n = a.size();
+  if (n <= 1) return;
+  std::vector<cld> ev(n / 2), od(n / 2);
+  for (size_t k = 0; k < n / 2; ++k) { ev[k] = a[2 * k]; od[k] = a[2 * k + 1]; }
+  host_fft(ev);
+  host_fft(od);
+  for (size_t k = 0; k < n / 2; ++k) {
+    cld t = root((int64_t)n, (int64_t)k) * od[k];
+    a[k] = ev[k] + t;
+    a[k + n / 2] = ev[k] - t;
+  }
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014): phase of the checksum vector
+uint64_t splitmix_mix(uint64_t z) {
+  z ^= z >> 30;
+  z *= 0xBF58476D1CE4E5B9ull;
+  z ^= z >> 27;
+  z *= 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// output-side encoding vector e: unit-modulus, seeded random phases
+std::vector<cld> encoding_vector(int ns) {
+  std::vector<cld> e(ns);
+  const uint64_t seed = 0x5EEDull;
+  for (int j = 0; j < ns; ++j) {
+    uint64_t w = splitmix_mix(seed + (uint64_t)(j + 1) * 0x9E3779B97F4A7C15ull);
+    ld theta = (ld)(w >> 11) * 0x1p-53L;
+    e[j] = cld(cosl(kTwoPi * theta), sinl(kTwoPi * theta));
+  }
+  return e;
+}
+
+template <typename R> struct DevC;
+template <> struct DevC<float> { typedef float2 t; };
+template <> struct DevC<double> { typedef double2 t; };
+
+template <typename R> std::vector<typename DevC<R>::t> round_table(const std::vector<cld>& v) {
+  std::vector<typename DevC<R>::t> out(v.size());
+  for (size_t i = 0; i < v.size(); ++i) {
+    out[i].x = (R)v[i].real();
+    out[i].y = (R)v[i].imag();
+  }
+  return out;
+}
+
+int ilog2_exact(int64_t n) {
+  int l = 0;
+  while (((int64_t)1 << l) < n) ++l;
+  return (((int64_t)1 << l) == n) ? l : -1;
+}
+
+// default threshold factor gamma per working precision: chosen from clean-run
+// residuals so that the largest clean |S1| stays far below tau
+const double kGamma[2] = {8.0, 16.0};
+const double kUnitRoundoff[2] = {0x1p-24, 0x1p-53};
+
+int g_num_sms = 0;
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// the plan
+// ---------------------------------------------------------------------------
+struct PassPlan {
+  const KernelEntry* ke = nullptr;
+  int kind = 0;
+  int ns = 0;
+  int grid = 0;
+  long long units_per_batch_item = 0;  // work units per transform (COL/ROW), SP: see units()
+  void* d_tw = nullptr;
+  void* d_ev = nullptr;
+  void* d_vv = nullptr;
+  double tau_coef = 0;
+};
+
+struct turbofft_plan {
+  int64_t n = 0, batch = 0;
+  int dtype = 0, direction = -1, ft_mode = 0;
+  int device = 0;
+  int num_passes = 1;
+  int n1 = 0, n2 = 1;
+  PassPlan pass[2];
+  void* d_tlo = nullptr;
+  void* d_thi = nullptr;
+  void* d_scratch = nullptr;
+  FtState* d_fts = nullptr;
+  FtState* h_fts = nullptr;
+  void* d_rec_sums = nullptr;
+  int rec_stride = 0;
+  tf::InjectSite armed{};
+  double threshold_scale = 1.0;
+  int T = 4;
+  cudaEvent_t done = nullptr;
+  bool have_exec = false;
+  std::string last_error;
+  int64_t workspace_bytes = 0;
+  // exec_host staging
+  void* h_stage_in[2] = {nullptr, nullptr};
+  void* h_stage_out[2] = {nullptr, nullptr};
+  void* h_scratch = nullptr;
+  int64_t chunk = 0;
+  cudaStream_t hs[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t hev[8] = {};
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+size_t elem_bytes(int dtype) { return dtype == TURBOFFT_C2C_F32 ? 8 : 16; }
+
+turbofft_status cuda_fail(turbofft_plan* p, cudaError_t e, const char* what) {
+  if (p) {
+    p->last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  }
+  return TURBOFFT_CUDA_ERROR;
+}
+
+bool dev_alloc(turbofft_plan* p, void** ptr, size_t bytes) {
+  if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return false;
+  }
+  p->allocs.push_back(*ptr);
+  p->workspace_bytes += (int64_t)bytes;
+  return true;
+}
+
+template <typename R>
+bool upload(turbofft_plan* p, void** dst, const std::vector<cld>& v) {
+  auto t = round_table<R>(v);
+  size_t bytes = t.size() * sizeof(t[0]);
+  if (!dev_alloc(p, dst, bytes)) return false;
+  return cudaMemcpy(*dst, t.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
+bool upload_tables(turbofft_plan* p, PassPlan& pp) {
+  const int ns = pp.ns;
+  std::vector<cld> tw(ns);
+  for (int q = 0; q < ns; ++q) tw[q] = root(ns, q);
+  std::vector<cld> e = encoding_vector(ns);
+  std::vector<cld> v = e;
+  host_fft(v);  // v = W e = (e^T W)^T, W symmetric (Eq. 1)
+  if (p->dtype == TURBOFFT_C2C_F32)
+    return upload<float>(p, &pp.d_tw, tw) && upload<float>(p, &pp.d_ev, e) && upload<float>(p, &pp.d_vv, v);
+  return upload<double>(p, &pp.d_tw, tw) && upload<double>(p, &pp.d_ev, e) && upload<double>(p, &pp.d_vv, v);
+}
+
+int occupancy_blocks(const KernelEntry* ke, bool ft) {
+  int nb = 0;
+  const void* fn = ft ? ke->fn_ft : ke->fn_plain;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, ke->nt, ke->smem_main) != cudaSuccess) {
+    cudaGetLastError();
+    nb = 1;
+  }
+  return std::max(1, nb);
+}
+
+bool set_smem_attrs(const KernelEntry* ke) {
+  // the attribute is per function; setting it again is harmless
+  if (cudaFuncSetAttribute(ke->fn_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, ke->smem_main) != cudaSuccess)
+    return false;
+  if (cudaFuncSetAttribute(ke->fn_ft, cudaFuncAttributeMaxDynamicSharedMemorySize, ke->smem_main) != cudaSuccess)
+    return false;
+  if (cudaFuncSetAttribute(ke->fn_fix, cudaFuncAttributeMaxDynamicSharedMemorySize, ke->smem_fix) != cudaSuccess)
+    return false;
+  return true;
+}
+
+long long units_for(const turbofft_plan* p, int pi, int64_t batch) {
+  const PassPlan& pp = p->pass[pi];
+  if (pp.kind == tf::KIND_SP) return (batch + pp.ke->s - 1) / pp.ke->s;
+  if (pp.kind == tf::KIND_COL) return batch * (p->n2 / pp.ke->s);
+  return batch * (p->n1 / pp.ke->s);
+}
+
+template <typename R>
+void fill_args(const turbofft_plan* p, int pi, const void* in, void* out, int64_t batch, int64_t tbase,
+               const tf::InjectSite& inj, tf::PassArgs<R>& A) {
+  typedef typename tf::CT<R>::c c;
+  const PassPlan& pp = p->pass[pi];
+  memset(&A, 0, sizeof(A));
+  A.in = static_cast<const c*>(in);
+  A.out = static_cast<c*>(out);
+  A.tw = static_cast<const c*>(pp.d_tw);
+  A.ev = static_cast<const c*>(pp.d_ev);
+  A.vv = static_cast<const c*>(pp.d_vv);
+  A.tlo = static_cast<const c*>(p->d_tlo);
+  A.thi = static_cast<const c*>(p->d_thi);
+  A.geo.n = p->n;
+  A.geo.n1 = p->n1;
+  A.geo.n2 = p->n2;
+  A.geo.batch = batch;
+  A.num_units = units_for(p, pi, batch);
+  const bool inverse = p->direction != TURBOFFT_FORWARD;
+  const bool last = (pi == p->num_passes - 1);
+  A.conj_in = (inverse && pi == 0) ? 1 : 0;
+  A.conj_out = (inverse && last) ? 1 : 0;
+  A.out_scale = (last && p->direction == TURBOFFT_INVERSE) ? (R)(1.0 / (double)p->n) : (R)1;
+  A.tau_coef = pp.tau_coef * p->threshold_scale;
+  A.ft = p->ft_mode;
+  A.T = p->T;
+  A.pass_id = pi;
+  A.transform_base = tbase;
+  A.fts = p->d_fts;
+  A.rec_sums = p->d_rec_sums;
+  A.rec_stride = p->rec_stride;
+  A.inj = inj;
+}
+
+// queue one transform of `batch` transforms (device pointers) on `stream`
+turbofft_status run(turbofft_plan* p, const void* in, void* out, void* scratch, int64_t batch, int64_t tbase,
+                    cudaStream_t stream, const tf::InjectSite& inj) {
+  const bool ft = p->ft_mode != TURBOFFT_FT_OFF;
+  for (int pi = 0; pi < p->num_passes; ++pi) {
+    const PassPlan& pp = p->pass[pi];
+    const void* pin = (pi == 0) ? in : scratch;
+    void* pout = (pi == p->num_passes - 1) ? out : scratch;
+    long long units = units_for(p, pi, batch);
+    int grid = (int)std::min<long long>(units, pp.grid);
+    if (grid < 1) grid = 1;
+    if (p->dtype == TURBOFFT_C2C_F32) {
+      tf::PassArgs<float> A;
+      fill_args<float>(p, pi, pin, pout, batch, tbase, inj, A);
+      (ft ? pp.ke->main_ft : pp.ke->main_plain)(&A, grid, stream);
+      if (ft) pp.ke->fix(&A, 8, stream);
+    } else {
+      tf::PassArgs<double> A;
+      fill_args<double>(p, pi, pin, pout, batch, tbase, inj, A);
+      (ft ? pp.ke->main_ft : pp.ke->main_plain)(&A, grid, stream);
+      if (ft) pp.ke->fix(&A, 8, stream);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(p, e, "kernel launch");
+  }
+  return TURBOFFT_SUCCESS;
+}
+
+bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* turbofft_status_string(turbofft_status s) {
+  switch (s) {
+    case TURBOFFT_SUCCESS: return "TURBOFFT_SUCCESS";
+    case TURBOFFT_INVALID_VALUE: return "TURBOFFT_INVALID_VALUE";
+    case TURBOFFT_UNSUPPORTED: return "TURBOFFT_UNSUPPORTED";
+    case TURBOFFT_ALLOC_FAILED: return "TURBOFFT_ALLOC_FAILED";
+    case TURBOFFT_CUDA_ERROR: return "TURBOFFT_CUDA_ERROR";
+    case TURBOFFT_FT_UNCORRECTABLE: return "TURBOFFT_FT_UNCORRECTABLE";
+    case TURBOFFT_TIMEOUT: return "TURBOFFT_TIMEOUT";
+  }
+  return "TURBOFFT_UNKNOWN_STATUS";
+}
+
+const char* turbofft_last_error(const turbofft_plan* p) { return p ? p->last_error.c_str() : ""; }
+
+turbofft_status turbofft_destroy(turbofft_plan* p) {
+  if (!p) return TURBOFFT_SUCCESS;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(p->device);
+  cudaDeviceSynchronize();
+  for (void* a : p->allocs) cudaFree(a);
+  if (p->h_fts) cudaFreeHost(p->h_fts);
+  if (p->done) cudaEventDestroy(p->done);
+  for (auto& s : p->hs)
+    if (s) cudaStreamDestroy(s);
+  for (auto& e : p->hev)
+    if (e) cudaEventDestroy(e);
+  cudaGetLastError();
+  cudaSetDevice(cur);
+  delete p;
+  return TURBOFFT_SUCCESS;
+}
+
+turbofft_status turbofft_plan_create(int64_t n, int64_t batch, turbofft_dtype dtype, int direction,
+                                     turbofft_ft_mode ft_mode, turbofft_plan** out) {
+  if (!out) return TURBOFFT_INVALID_VALUE;
+  *out = nullptr;
+  const int logn = ilog2_exact(n);
+  if (logn < 3 || logn > 24) return TURBOFFT_INVALID_VALUE;
+  if (batch < 1 || batch * n > ((int64_t)1 << 31)) return TURBOFFT_INVALID_VALUE;
+  if (dtype != TURBOFFT_C2C_F32 && dtype != TURBOFFT_C2C_F64) return TURBOFFT_INVALID_VALUE;
+  if (direction != TURBOFFT_FORWARD && direction != TURBOFFT_INVERSE && direction != TURBOFFT_INVERSE_UNSCALED)
+    return TURBOFFT_INVALID_VALUE;
+  if (ft_mode != TURBOFFT_FT_OFF && ft_mode != TURBOFFT_FT_DETECT && ft_mode != TURBOFFT_FT_CORRECT)
+    return TURBOFFT_INVALID_VALUE;
+
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    return TURBOFFT_CUDA_ERROR;
+  }
+  if (g_num_sms == 0) {
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  const Registry& reg = registry();
+  turbofft_plan* p = new turbofft_plan();
+  p->n = n;
+  p->batch = batch;
+  p->dtype = dtype;
+  p->direction = direction;
+  p->ft_mode = ft_mode;
+  p->device = dev;
+  const int dt = dtype == TURBOFFT_C2C_F32 ? 0 : 1;
+
+  // pass split: one pass up to the largest single-pass size, else N1 x N2
+  if (n <= reg.max_sp(dt)) {
+    p->num_passes = 1;
+    p->n1 = (int)n;
+    p->n2 = 1;
+    p->pass[0].kind = tf::KIND_SP;
+    p->pass[0].ns = (int)n;
+  } else {
+    p->num_passes = 2;
+    p->n1 = 1 << (logn / 2);
+    p->n2 = 1 << (logn - logn / 2);
+    p->pass[0].kind = tf::KIND_COL;
+    p->pass[0].ns = p->n1;
+    p->pass[1].kind = tf::KIND_ROW;
+    p->pass[1].ns = p->n2;
+  }
+  for (int pi = 0; pi < p->num_passes; ++pi) {
+    PassPlan& pp = p->pass[pi];
+    pp.ke = reg.find(dt, pp.kind, pp.ns);
+    if (!pp.ke) {
+      delete p;
+      return TURBOFFT_UNSUPPORTED;
+    }
+    if (!set_smem_attrs(pp.ke)) {
+      cudaGetLastError();
+      delete p;
+      return TURBOFFT_CUDA_ERROR;
+    }
+    const int occ = occupancy_blocks(pp.ke, ft_mode != TURBOFFT_FT_OFF);
+    pp.grid = occ * g_num_sms;
+    pp.tau_coef = kGamma[dt] * kUnitRoundoff[dt] * sqrt((double)ilog2_exact(pp.ns));
+    if (!upload_tables(p, pp)) {
+      turbofft_destroy(p);
+      return TURBOFFT_ALLOC_FAILED;
+    }
+  }
+  if (p->num_passes == 2) {
+    // inter-pass twiddles w_N^q = thi[q >> 12] * tlo[q & 4095]
+    std::vector<cld> lo(4096), hi((size_t)std::max<int64_t>(1, n / 4096));
+    for (int j = 0; j < 4096; ++j) lo[j] = root(n, j);
+    for (size_t j = 0; j < hi.size(); ++j) hi[j] = root(n, (int64_t)j * 4096);
+    bool ok = (dt == 0) ? (upload<float>(p, &p->d_tlo, lo) && upload<float>(p, &p->d_thi, hi))
+                        : (upload<double>(p, &p->d_tlo, lo) && upload<double>(p, &p->d_thi, hi));
+    if (!ok || !dev_alloc(p, &p->d_scratch, (size_t)(batch * n) * elem_bytes(dtype))) {
+      turbofft_destroy(p);
+      return TURBOFFT_ALLOC_FAILED;
+    }
+  }
+  if (ft_mode != TURBOFFT_FT_OFF) {
+    void* fts = nullptr;
+    if (!dev_alloc(p, &fts, sizeof(FtState))) {
+      turbofft_destroy(p);
+      return TURBOFFT_ALLOC_FAILED;
+    }
+    p->d_fts = static_cast<FtState*>(fts);
+    if (cudaMemset(p->d_fts, 0, sizeof(FtState)) != cudaSuccess ||
+        cudaHostAlloc((void**)&p->h_fts, sizeof(FtState), cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      turbofft_destroy(p);
+      return TURBOFFT_ALLOC_FAILED;
+    }
+    memset(p->h_fts, 0, sizeof(FtState));
+    p->rec_stride = std::max(p->pass[0].ns, p->num_passes == 2 ? p->pass[1].ns : 0);
+    if (!dev_alloc(p, &p->d_rec_sums, (size_t)tf::MAX_RECORDS * 2 * p->rec_stride * elem_bytes(dtype))) {
+      turbofft_destroy(p);
+      return TURBOFFT_ALLOC_FAILED;
+    }
+  }
+  if (cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    turbofft_destroy(p);
+    return TURBOFFT_CUDA_ERROR;
+  }
+  *out = p;
+  return TURBOFFT_SUCCESS;
+}
+
+turbofft_status turbofft_plan_get_info(const turbofft_plan* p, turbofft_plan_info* info) {
+  if (!p || !info) return TURBOFFT_INVALID_VALUE;
+  memset(info, 0, sizeof(*info));
+  info->n = p->n;
+  info->batch = p->batch;
+  info->dtype = p->dtype;
+  info->direction = p->direction;
+  info->ft_mode = p->ft_mode;
+  info->num_passes = p->num_passes;
+  for (int pi = 0; pi < p->num_passes; ++pi) {
+    info->sub_n[pi] = p->pass[pi].ns;
+    info->stages[pi] = p->pass[pi].ke->stages;
+    info->radix[pi] = p->pass[pi].ke->e;
+    info->grid[pi] = p->pass[pi].grid;
+    info->block[pi] = p->pass[pi].ke->nt;
+  }
+  if (p->num_passes == 1) info->sub_n[1] = 1;
+  info->group_transactions = p->T;
+  info->workspace_bytes = p->workspace_bytes;
+  return TURBOFFT_SUCCESS;
+}
+
+turbofft_status turbofft_set_threshold_scale(turbofft_plan* p, double factor) {
+  if (!p || !(factor > 0) || !isfinite(factor)) return TURBOFFT_INVALID_VALUE;
+  p->threshold_scale = factor;
+  return TURBOFFT_SUCCESS;
+}
+
+turbofft_status turbofft_inject(turbofft_plan* p, turbofft_site site, int bit) {
+  if (!p) return TURBOFFT_INVALID_VALUE;
+  const int nbits = p->dtype == TURBOFFT_C2C_F32 ? 32 : 64;
+  if (bit < 0 || bit >= nbits) return TURBOFFT_INVALID_VALUE;
+  if (site.transform < 0 || site.transform >= p->batch) return TURBOFFT_INVALID_VALUE;
+  if (site.pass < 0 || site.pass >= p->num_passes) return TURBOFFT_INVALID_VALUE;
+  if (site.stage < 0 || site.stage > p->pass[site.pass].ke->stages) return TURBOFFT_INVALID_VALUE;
+  if (site.element < 0 || site.element >= p->n) return TURBOFFT_INVALID_VALUE;
+  if (site.component != 0 && site.component != 1) return TURBOFFT_INVALID_VALUE;
+  tf::InjectSite s{};
+  s.active = 1;
+  s.pass = site.pass;
+  s.stage = site.stage;
+  s.comp = site.component;
+  s.bit = bit;
+  const int kind = p->pass[site.pass].kind;
+  if (kind == tf::KIND_SP) {
+    s.signal = site.transform;
+    s.pos = (int)site.element;
+  } else if (kind == tf::KIND_COL) {
+    s.signal = site.transform * p->n2 + site.element % p->n2;
+    s.pos = (int)(site.element / p->n2);
+  } else {
+    s.signal = site.transform * p->n1 + site.element / p->n2;
+    s.pos = (int)(site.element % p->n2);
+  }
+  p->armed = s;
+  return TURBOFFT_SUCCESS;
+}
+
+turbofft_status turbofft_exec(turbofft_plan* p, const void* in, void* out, turbofft_stream stream) {
+  if (!p || !in || !out) return TURBOFFT_INVALID_VALUE;
+  if (!aligned16(in) || !aligned16(out)) return TURBOFFT_INVALID_VALUE;
+  const size_t bytes = (size_t)(p->batch * p->n) * elem_bytes(p->dtype);
+  const char* a = static_cast<const char*>(in);
+  const char* b = static_cast<const char*>(out);
+  if (a < b + bytes && b < a + bytes) return TURBOFFT_UNSUPPORTED;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const bool ft = p->ft_mode != TURBOFFT_FT_OFF;
+  if (ft) {
+    cudaError_t e = cudaMemsetAsync(p->d_fts, 0, tf::FT_HEADER_BYTES, s);
+    if (e != cudaSuccess) return cuda_fail(p, e, "report reset");
+  }
+  tf::InjectSite inj = p->armed;
+  p->armed.active = 0;
+  turbofft_status st = run(p, in, out, p->d_scratch, p->batch, 0, s, inj);
+  if (st != TURBOFFT_SUCCESS) return st;
+  if (ft) {
+    cudaError_t e = cudaMemcpyAsync(p->h_fts, p->d_fts, sizeof(FtState), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(p, e, "report copy");
+  }
+  cudaError_t e = cudaEventRecord(p->done, s);
+  if (e != cudaSuccess) return cuda_fail(p, e, "event record");
+  p->have_exec = true;
+  return TURBOFFT_SUCCESS;
+}
+
+turbofft_status turbofft_exec_host(turbofft_plan* p, const void* host_in, void* host_out, turbofft_stream stream) {
+  if (!p || !host_in || !host_out) return TURBOFFT_INVALID_VALUE;
+  const size_t eb = elem_bytes(p->dtype);
+  cudaError_t e;
+  if (!p->hs[0]) {
+    // chunk: about 1/8 of the batch, at least 32 MiB when the batch allows
+    int64_t per = p->n * (int64_t)eb;
+    int64_t chunk = std::max<int64_t>(1, p->batch / 8);
+    chunk = std::max<int64_t>(chunk, std::min<int64_t>(p->batch, ((int64_t)32 << 20) / per));
+    p->chunk = chunk;
+    for (int i = 0; i < 2; ++i) {
+      if (!dev_alloc(p, &p->h_stage_in[i], (size_t)(chunk * p->n) * eb) ||
+          !dev_alloc(p, &p->h_stage_out[i], (size_t)(chunk * p->n) * eb))
+        return TURBOFFT_ALLOC_FAILED;
+    }
+    if (p->num_passes == 2 && !dev_alloc(p, &p->h_scratch, (size_t)(chunk * p->n) * eb)) return TURBOFFT_ALLOC_FAILED;
+    for (int i = 0; i < 3; ++i)
+      if ((e = cudaStreamCreateWithFlags(&p->hs[i], cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(p, e, "stream create");
+    for (int i = 0; i < 8; ++i)
+      if ((e = cudaEventCreateWithFlags(&p->hev[i], cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(p, e, "event create");
+  }
+  cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+  cudaStream_t sh = p->hs[0], sc = p->hs[1], sd = p->hs[2];
+  // hev[0..1] h2d done, hev[2..3] compute done, hev[4..5] d2h done, hev[6] start
+  if ((e = cudaEventRecord(p->hev[6], user)) != cudaSuccess) return cuda_fail(p, e, "event record");
+  cudaStreamWaitEvent(sh, p->hev[6], 0);
+  cudaStreamWaitEvent(sc, p->hev[6], 0);
+  cudaStreamWaitEvent(sd, p->hev[6], 0);
+  const bool ft = p->ft_mode != TURBOFFT_FT_OFF;
+  if (ft && (e = cudaMemsetAsync(p->d_fts, 0, tf::FT_HEADER_BYTES, sc)) != cudaSuccess)
+    return cuda_fail(p, e, "report reset");
+  tf::InjectSite inj = p->armed;
+  p->armed.active = 0;
+  const char* hin = static_cast<const char*>(host_in);
+  char* hout = static_cast<char*>(host_out);
+  int ci = 0;
+  for (int64_t b0 = 0; b0 < p->batch; b0 += p->chunk, ++ci) {
+    const int sl = ci & 1;
+    const int64_t nb = std::min<int64_t>(p->chunk, p->batch - b0);
+    const size_t off = (size_t)(b0 * p->n) * eb, bytes = (size_t)(nb * p->n) * eb;
+    if (ci >= 2) cudaStreamWaitEvent(sh, p->hev[2 + sl], 0);  // stage-in slot consumed
+    if ((e = cudaMemcpyAsync(p->h_stage_in[sl], hin + off, bytes, cudaMemcpyHostToDevice, sh)) != cudaSuccess)
+      return cuda_fail(p, e, "h2d");
+    cudaEventRecord(p->hev[sl], sh);
+    cudaStreamWaitEvent(sc, p->hev[sl], 0);
+    if (ci >= 2) cudaStreamWaitEvent(sc, p->hev[4 + sl], 0);  // stage-out slot drained
+    tf::InjectSite cinj = inj;
+    if (inj.active) {
+      // the armed transform belongs to exactly one chunk
+      int64_t tr = -1;
+      const int kind = p->pass[inj.pass].kind;
+      if (kind == tf::KIND_SP) tr = inj.signal;
+      else if (kind == tf::KIND_COL) tr = inj.signal / p->n2;
+      else tr = inj.signal / p->n1;
+      if (tr >= b0 && tr < b0 + nb) {
+        int64_t per = (kind == tf::KIND_SP) ? 1 : (kind == tf::KIND_COL ? p->n2 : p->n1);
+        cinj.signal = inj.signal - b0 * per;
+      } else {
+        cinj.active = 0;
+      }
+    }
+    turbofft_status st = run(p, p->h_stage_in[sl], p->h_stage_out[sl], p->h_scratch, nb, b0, sc, cinj);
+    if (st != TURBOFFT_SUCCESS) return st;
+    cudaEventRecord(p->hev[2 + sl], sc);
+    cudaStreamWaitEvent(sd, p->hev[2 + sl], 0);
+    if ((e = cudaMemcpyAsync(hout + off, p->h_stage_out[sl], bytes, cudaMemcpyDeviceToHost, sd)) != cudaSuccess)
+      return cuda_fail(p, e, "d2h");
+    cudaEventRecord(p->hev[4 + sl], sd);
+  }
+  if (ft) {
+    cudaStreamWaitEvent(sc, p->hev[4 + ((ci - 1) & 1)], 0);
+    if ((e = cudaMemcpyAsync(p->h_fts, p->d_fts, sizeof(FtState), cudaMemcpyDeviceToHost, sc)) != cudaSuccess)
+      return cuda_fail(p, e, "report copy");
+    cudaEventRecord(p->hev[7], sc);
+    cudaStreamWaitEvent(sd, p->hev[7], 0);
+  }
+  cudaEventRecord(p->done, sd);
+  cudaStreamWaitEvent(user, p->done, 0);
+  p->have_exec = true;
+  if ((e = cudaEventSynchronize(p->done)) != cudaSuccess) return cuda_fail(p, e, "exec_host");
+  return TURBOFFT_SUCCESS;
+}
+
+turbofft_status turbofft_get_report(turbofft_plan* p, turbofft_report* r) {
+  if (!p || !r) return TURBOFFT_INVALID_VALUE;
+  memset(r, 0, sizeof(*r));
+  r->first_transform = -1;
+  r->first_pass = -1;
+  if (p->ft_mode == TURBOFFT_FT_OFF || !p->have_exec) return TURBOFFT_SUCCESS;
+  cudaError_t e = cudaEventSynchronize(p->done);
+  if (e != cudaSuccess) return cuda_fail(p, e, "report wait");
+  const FtState& h = *p->h_fts;
+  r->groups_checked = (int64_t)h.groups;
+  r->detected = (int64_t)h.detected;
+  r->located = (int64_t)h.located;
+  r->corrected = (int64_t)h.corrected;
+  r->recomputed = (int64_t)h.recomputed;
+  r->uncorrectable = (int64_t)(h.uncorrectable + h.dropped);
+  r->max_clean_ratio = h.max_clean_ratio;
+  const int nrec = (int)std::min<unsigned long long>(h.num_records, tf::MAX_RECORDS);
+  for (int i = 0; i < nrec; ++i) {
+    const FtRecord& rc = h.rec[i];
+    if (r->first_pass < 0) {
+      r->first_pass = rc.pass_id;
+      r->first_residual = sqrt(rc.s1r * rc.s1r + rc.s1i * rc.s1i);
+      r->first_threshold = rc.tau;
+    }
+    if (rc.signal >= 0 && r->first_transform < 0) {
+      const int kind = p->pass[rc.pass_id].kind;
+      int64_t tr = rc.signal;
+      if (kind == tf::KIND_COL) tr = rc.signal / p->n2;
+      if (kind == tf::KIND_ROW) tr = rc.signal / p->n1;
+      r->first_transform = tr + rc.transform_base;
+    }
+  }
+  if (r->uncorrectable > 0) return TURBOFFT_FT_UNCORRECTABLE;
+  if (p->ft_mode == TURBOFFT_FT_DETECT && r->detected > 0) return TURBOFFT_FT_UNCORRECTABLE;
+  return TURBOFFT_SUCCESS;
+}
+
+}  // extern "C"

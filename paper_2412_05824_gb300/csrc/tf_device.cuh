@@ -1,0 +1,872 @@
+// Device code of the batched complex FFT with fused two-sided ABFT.
+//
+// Transform (TurboFFT Sec. 2.2.1 definition; Sec. 3.1 tiling; Sec. 3.2
+// Stockham autosort with a padding-free, swizzled shared-memory exchange):
+//   A length-NS sub-transform is held by P = NS/E threads, E complex values
+//   per thread in registers.  Thread t always holds the "home" positions
+//   t + i*P, i < E.  The transform runs as Stockham radix passes; pass p has
+//   radix R (E, or a smaller radix for the last pass) and sub-transform
+//   length L = E^p before it.  In pass p thread t computes E/R butterflies
+//   j = t + u*P: inputs X[j + m*NS/R] (exactly its home registers),
+//   twiddle w_{L*R}^{(j mod L)*m}, a radix-R DFT in registers, outputs to
+//   Y[(j div L)*L*R + (j mod L) + m*L].  Every pass but the last writes Y to
+//   shared memory and reads its home positions back; the last pass's
+//   outputs land in the thread's own home registers.
+//
+// Kernel kinds:
+//   KIND_SP   one pass over HBM, S whole transforms per transaction
+//   KIND_COL  first pass of the four-step plan N = N1*N2: S adjacent
+//             columns (stride N2) per transaction, length-N1 FFTs, then the
+//             inter-pass twiddle w_N^{k1*n2}
+//   KIND_ROW  second pass: S adjacent rows (contiguous) per transaction,
+//             length-N2 FFTs, transposed store y[k1 + N1*k2] through shared
+//             memory so that global stores stay coalesced
+//
+// Fault tolerance (TurboFFT Sec. 4.1-4.3), per thread block, per slot:
+//   a checksum group is the T consecutive transactions a block processes;
+//   per transaction each thread accumulates its share of
+//       r = e . y_hat - v . x       (left checksum, v = W^T e, Eq. 1-2)
+//   into S1 += r and S2 += (g+1) r  (location encoding, Sec. 4.1 / 4.3)
+//   and the right-side sums x_bar += x, y_bar += y_hat (Eq. 4-5).  At the
+//   end of a group the block reduces S1, S2 and the input energy (warp
+//   shuffles in the working precision, cross-warp in float64), compares
+//   |S1| with tau = gamma u sqrt(log2 NS) sqrt(NS * energy) in float64 and,
+//   on a mismatch, appends a record (location and right-side sums) that the
+//   correction kernel consumes right after this pass (delayed, batched
+//   correction, Sec. 4.1.2).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+#include <utility>
+
+#include "tf_dft_constants.h"
+#include "tf_types.h"
+
+namespace tf {
+
+// ---------------------------------------------------------------------------
+// complex helpers
+// ---------------------------------------------------------------------------
+template <typename R> struct CT;
+template <> struct CT<float> { using c = float2; };
+template <> struct CT<double> { using c = double2; };
+
+template <typename C> __device__ __forceinline__ C mk(decltype(C::x) a, decltype(C::x) b) {
+  C r; r.x = a; r.y = b; return r;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { return mk<C>(a.x, -a.y); }
+template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return mk<C>(a.x * s, a.y * s); }
+// acc += a*b
+template <typename C> __device__ __forceinline__ void cmac(C& acc, C a, C b) {
+  acc.x += a.x * b.x - a.y * b.y;
+  acc.y += a.x * b.y + a.y * b.x;
+}
+
+template <typename C> __device__ __forceinline__ C ldg(const C* p) { return __ldg(p); }
+
+template <int N> struct ILog2 { static constexpr int v = 1 + ILog2<N / 2>::v; };
+template <> struct ILog2<1> { static constexpr int v = 0; };
+
+template <int I> using IC = std::integral_constant<int, I>;
+template <int B, int E, class F> __device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (B < E) {
+    f(IC<B>{});
+    static_for<B + 1, E>(f);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// register-level radix-R DFT (R <= 32), forward sign, natural order in/out.
+// Radix-2 decimation in time, applied recursively; constant twiddles
+// w_R^k = cos(2 pi k/R) - i sin(2 pi k/R) are compile-time immediates, and the
+// trivial ones (1, -i, (1-i)/sqrt2, (-1-i)/sqrt2) are special-cased.
+// ---------------------------------------------------------------------------
+template <typename C, int R, int K> __device__ __forceinline__ C twc(C v) {
+  using T = decltype(C::x);
+  constexpr int q = K * (32 / R);  // index into the 32-point circle
+  if constexpr (q == 0) {
+    return v;
+  } else if constexpr (q == 8) {  // -i
+    return mk<C>(v.y, -v.x);
+  } else if constexpr (q == 4) {  // (1 - i)/sqrt2
+    constexpr T s = (T)0.707106781186547524401;
+    return mk<C>((v.x + v.y) * s, (v.y - v.x) * s);
+  } else if constexpr (q == 12) {  // (-1 - i)/sqrt2
+    constexpr T s = (T)0.707106781186547524401;
+    return mk<C>((v.y - v.x) * s, -(v.x + v.y) * s);
+  } else {
+    constexpr T c = (T)cos32(q), s = (T)sin32(q);
+    // (a + ib)(c - is) = (ac + bs) + i(bc - as)
+    return mk<C>(v.x * c + v.y * s, v.y * c - v.x * s);
+  }
+}
+
+template <typename C, int R> struct Dft {
+  static __device__ __forceinline__ void run(C* x) {
+    C ev[R / 2], od[R / 2];
+#pragma unroll
+    for (int k = 0; k < R / 2; ++k) { ev[k] = x[2 * k]; od[k] = x[2 * k + 1]; }
+    Dft<C, R / 2>::run(ev);
+    Dft<C, R / 2>::run(od);
+    static_for<0, R / 2>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      C t = twc<C, R, k>(od[k]);
+      x[k] = cadd(ev[k], t);
+      x[k + R / 2] = csub(ev[k], t);
+    });
+  }
+};
+template <typename C> struct Dft<C, 1> { static __device__ __forceinline__ void run(C*) {} };
+template <typename C> struct Dft<C, 2> {
+  static __device__ __forceinline__ void run(C* x) {
+    C a = x[0], b = x[1];
+    x[0] = cadd(a, b);
+    x[1] = csub(a, b);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// compile-time configuration of one kernel
+// ---------------------------------------------------------------------------
+template <typename R_, int NS_, int E_, int S_, int KIND_>
+struct Cfg {
+  using real = R_;
+  using c = typename CT<R_>::c;
+  static constexpr int NS = NS_;
+  static constexpr int E = E_;
+  static constexpr int S = S_;
+  static constexpr int KIND = KIND_;
+  static constexpr int P = NS / E;
+  static constexpr int NT = P * S;
+  static constexpr bool SLOT_FAST = (KIND == KIND_COL);
+  static constexpr int LOG_NS = ILog2<NS>::v;
+  static constexpr int LOG_E = ILog2<E>::v;
+  static constexpr int NP = (LOG_NS + LOG_E - 1) / LOG_E;   // radix passes
+  static constexpr int LOG_RL = LOG_NS - (NP - 1) * LOG_E;  // log radix of the last pass
+  static constexpr int B = (sizeof(c) == 8) ? 4 : 3;         // 128-byte bank row, in elements
+  static constexpr int SMEM_BYTES = S * NS * (int)sizeof(c);
+  static_assert(E <= NS && NS % E == 0, "E must divide NS");
+  static_assert(NT >= 32 && NT <= 1024 && NT % 32 == 0, "block size");
+  static_assert(!SLOT_FAST || (32 % S == 0), "slot-fast mapping needs S | 32");
+};
+
+template <class K, int p> struct PassInfo {
+  static constexpr int LOG_R = (p == K::NP - 1) ? K::LOG_RL : K::LOG_E;
+  static constexpr int R = 1 << LOG_R;
+  static constexpr int NB = K::E / R;           // butterflies per thread
+  static constexpr int LOG_L = p * K::LOG_E;
+  static constexpr int L = 1 << LOG_L;
+  static constexpr bool LAST = (p == K::NP - 1);
+  static constexpr int TWS = K::NS / (L * R);   // twiddle table stride
+};
+
+// Shared-memory index of (slot, pos) in the exchange written by pass p.
+// Slot-major layouts XOR bits [l, B) of the position with bits
+// [l + r, l + r + B - l) when the pass writes with a stride (l < B): a
+// padding-free swizzle that keeps both the pass's scattered writes and the
+// next pass's contiguous reads free of bank conflicts (Sec. 3.2).
+template <class K, int p> __device__ __forceinline__ int sidx(int slot, int pos) {
+  if constexpr (K::SLOT_FAST) {
+    return pos * K::S + slot;
+  } else {
+    constexpr int l = PassInfo<K, p>::LOG_L, r = PassInfo<K, p>::LOG_R;
+    int q = pos;
+    if constexpr (l < K::B && l + r >= K::B) q ^= ((pos >> (l + r)) & ((1 << (K::B - l)) - 1)) << l;
+    return slot * K::NS + q;
+  }
+}
+
+// Injection context of one thread for the current transaction.
+struct InjCtx {
+  bool on;
+  int stage, pos, comp, bit;
+};
+
+__device__ __forceinline__ float flip1(float f, int bit) { return __uint_as_float(__float_as_uint(f) ^ (1u << bit)); }
+__device__ __forceinline__ double flip1(double f, int bit) {
+  return __longlong_as_double(__double_as_longlong(f) ^ (1ll << bit));
+}
+template <typename C> __device__ __forceinline__ void flip_bit(C& v, int comp, int bit) {
+  if (comp) v.y = flip1(v.y, bit);
+  else v.x = flip1(v.x, bit);
+}
+
+template <class K> __device__ __forceinline__ void inject_stage(typename K::c (&a)[K::E], int stage,
+                                                                const InjCtx& ic, int t) {
+  if (ic.on && ic.stage == stage) {
+#pragma unroll
+    for (int i = 0; i < K::E; ++i)
+      if (t + i * K::P == ic.pos) flip_bit(a[i], ic.comp, ic.bit);
+  }
+}
+
+template <class K, int p>
+__device__ __forceinline__ void run_pass(typename K::c (&a)[K::E], typename K::c* sm,
+                                         const typename K::c* __restrict__ tw, int slot, int t) {
+  using c = typename K::c;
+  using PI = PassInfo<K, p>;
+  constexpr int R = PI::R, NB = PI::NB, L = PI::L;
+#pragma unroll
+  for (int u = 0; u < NB; ++u) {
+    const int j = t + u * K::P;
+    const int k = j & (L - 1);
+    c b[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) b[m] = a[u + m * NB];
+    if constexpr (L > 1) {
+#pragma unroll
+      for (int m = 1; m < R; ++m) b[m] = cmul(b[m], ldg(tw + PI::TWS * k * m));
+    }
+    Dft<c, R>::run(b);
+    if constexpr (PI::LAST) {
+#pragma unroll
+      for (int m = 0; m < R; ++m) a[u + m * NB] = b[m];
+    } else {
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int m = 0; m < R; ++m) sm[sidx<K, p>(slot, base + m * L)] = b[m];
+    }
+  }
+  if constexpr (!PI::LAST) {
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < K::E; ++i) a[i] = sm[sidx<K, p>(slot, t + i * K::P)];
+    __syncthreads();
+  }
+}
+
+template <class K, int p, bool END = (p == K::NP)> struct Passes {
+  static __device__ __forceinline__ void run(typename K::c (&a)[K::E], typename K::c* sm,
+                                             const typename K::c* __restrict__ tw, int slot, int t,
+                                             const InjCtx& ic) {
+    inject_stage<K>(a, p, ic, t);
+    run_pass<K, p>(a, sm, tw, slot, t);
+    Passes<K, p + 1>::run(a, sm, tw, slot, t, ic);
+  }
+};
+template <class K, int p> struct Passes<K, p, true> {
+  static __device__ __forceinline__ void run(typename K::c (&a)[K::E], typename K::c*,
+                                             const typename K::c* __restrict__, int, int t,
+                                             const InjCtx& ic) {
+    inject_stage<K>(a, p, ic, t);
+  }
+};
+
+// full sub-transform in registers + shared memory (all threads of the block
+// take part; no injection)
+template <class K>
+__device__ __forceinline__ void fft_block(typename K::c (&a)[K::E], typename K::c* sm,
+                                          const typename K::c* __restrict__ tw, int slot, int t) {
+  InjCtx off{false, 0, 0, 0, 0};
+  Passes<K, 0>::run(a, sm, tw, slot, t, off);
+}
+
+// ---------------------------------------------------------------------------
+// addressing of one sub-transform ("signal") of a pass
+// ---------------------------------------------------------------------------
+struct Geo {
+  long long n;   // full transform length N
+  int n1, n2;    // N = n1 * n2 (single pass: n1 = N, n2 = 1)
+  long long batch;
+};
+
+// signal id of slot `slot` of work unit `unit`; -1 if past the end (ragged tail)
+template <class K> __device__ __forceinline__ long long signal_of(const Geo& g, long long unit, int slot) {
+  if constexpr (K::KIND == KIND_SP) {
+    long long s = unit * K::S + slot;
+    return s < g.batch ? s : -1;
+  } else if constexpr (K::KIND == KIND_COL) {
+    const int blocks = g.n2 / K::S;
+    long long b = unit / blocks;
+    int n2 = (int)(unit - b * blocks) * K::S + slot;
+    return b * g.n2 + n2;
+  } else {
+    const int blocks = g.n1 / K::S;
+    long long b = unit / blocks;
+    int k1 = (int)(unit - b * blocks) * K::S + slot;
+    return b * g.n1 + k1;
+  }
+}
+
+// element offset of position `pos` of signal `sig` in this pass's input
+template <class K> __device__ __forceinline__ long long in_off(const Geo& g, long long sig, int pos) {
+  if constexpr (K::KIND == KIND_SP) {
+    return sig * g.n + pos;
+  } else if constexpr (K::KIND == KIND_COL) {
+    long long b = sig / g.n2;
+    int n2 = (int)(sig - b * g.n2);
+    return b * g.n + (long long)pos * g.n2 + n2;
+  } else {
+    long long b = sig / g.n1;
+    int k1 = (int)(sig - b * g.n1);
+    return b * g.n + (long long)k1 * g.n2 + pos;
+  }
+}
+
+// element offset of output position `pos` of signal `sig` in this pass's output
+template <class K> __device__ __forceinline__ long long out_off(const Geo& g, long long sig, int pos) {
+  if constexpr (K::KIND == KIND_ROW) {
+    long long b = sig / g.n1;
+    int k1 = (int)(sig - b * g.n1);
+    return b * g.n + k1 + (long long)g.n1 * pos;
+  } else {
+    return in_off<K>(g, sig, pos);
+  }
+}
+
+// inter-pass twiddle w_N^{k1 * n2} for column n2 of signal `sig` (KIND_COL):
+// w_N^q = thi[q >> 12] * tlo[q & 4095]
+template <class K> __device__ __forceinline__ typename K::c colTwiddle(const Geo& g, const typename K::c* tlo,
+                                                                       const typename K::c* thi, long long sig,
+                                                                       int k1) {
+  long long b = sig / g.n2;
+  int n2 = (int)(sig - b * g.n2);
+  unsigned q = (unsigned)k1 * (unsigned)n2;
+  return cmul(ldg(thi + (q >> 12)), ldg(tlo + (q & 4095u)));
+}
+
+// ---------------------------------------------------------------------------
+// kernel arguments
+// ---------------------------------------------------------------------------
+template <typename R> struct PassArgs {
+  using c = typename CT<R>::c;
+  const c* in;
+  c* out;
+  const c* tw;    // w_NS^q, q < NS (forward sign)
+  const c* ev;    // output-side encoding vector e, NS entries
+  const c* vv;    // input-side vector v = W^T e, NS entries
+  const c* tlo;   // inter-pass twiddles (KIND_COL)
+  const c* thi;
+  Geo geo;
+  long long num_units;
+  int conj_in;    // inverse: conjugate on load (first pass)
+  int conj_out;   // inverse: conjugate on store (last pass)
+  R out_scale;    // 1 or 1/N on store (last pass)
+  double tau_coef;  // gamma * u * sqrt(log2 NS) * threshold scale
+  int ft;         // FT_OFF / FT_DETECT / FT_CORRECT
+  int T;          // transactions per checksum group
+  int pass_id;
+  long long transform_base;  // first transform of this launch in the caller's batch
+  FtState* fts;
+  void* rec_sums; // MAX_RECORDS x 2 x NS_MAX complex (x_bar, y_bar)
+  int rec_stride; // complex elements per record half (NS_MAX)
+  InjectSite inj;
+};
+
+// ---------------------------------------------------------------------------
+// block reduction helpers for the checksum group
+// ---------------------------------------------------------------------------
+template <class K> struct Seg {
+  // lanes of one slot inside a warp: pos-fast -> contiguous runs of min(P,32);
+  // slot-fast -> lanes congruent mod S.
+  static constexpr int RUN = (K::P < 32) ? K::P : 32;
+  static constexpr int PER_WARP = K::SLOT_FAST ? K::S : (32 / RUN);
+  static constexpr int COUNT = (K::NT / 32) * PER_WARP;
+};
+
+template <class K, typename V> __device__ __forceinline__ V seg_reduce_sum(V v) {
+  if constexpr (K::SLOT_FAST) {
+#pragma unroll
+    for (int o = K::S; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  } else {
+#pragma unroll
+    for (int o = 1; o < Seg<K>::RUN; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+template <class K> __device__ __forceinline__ int seg_reduce_min(int v) {
+  if constexpr (K::SLOT_FAST) {
+#pragma unroll
+    for (int o = K::S; o < 32; o <<= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  } else {
+#pragma unroll
+    for (int o = 1; o < Seg<K>::RUN; o <<= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  }
+  return v;
+}
+template <class K> __device__ __forceinline__ int seg_reduce_max(int v) {
+  if constexpr (K::SLOT_FAST) {
+#pragma unroll
+    for (int o = K::S; o < 32; o <<= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  } else {
+#pragma unroll
+    for (int o = 1; o < Seg<K>::RUN; o <<= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  }
+  return v;
+}
+// is this lane the leader of its segment, and the segment id
+template <class K> __device__ __forceinline__ bool seg_leader(int tid, int& seg) {
+  const int lane = tid & 31, warp = tid >> 5;
+  if constexpr (K::SLOT_FAST) {
+    seg = warp * K::S + lane;
+    return lane < K::S;
+  } else {
+    seg = warp * Seg<K>::PER_WARP + lane / Seg<K>::RUN;
+    return (lane % Seg<K>::RUN) == 0;
+  }
+}
+// segments that hold slot s: calls f(seg) for each
+template <class K, class F> __device__ __forceinline__ void for_slot_segments(int s, F&& f) {
+  if constexpr (K::SLOT_FAST) {
+    for (int w = 0; w < K::NT / 32; ++w) f(w * K::S + s);
+  } else if constexpr (K::P >= 32) {
+    for (int w = 0; w < K::P / 32; ++w) f(s * (K::P / 32) + w);
+  } else {
+    f(s);
+  }
+}
+
+// dynamic shared memory of the transform kernel: the exchange buffer, which
+// the checksum-group reduction reuses
+template <class K> constexpr int pass_smem_bytes() {
+  return (K::SMEM_BYTES > Seg<K>::COUNT * 64 + K::S * 4) ? K::SMEM_BYTES : (Seg<K>::COUNT * 64 + K::S * 4);
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(float* addr, float v) {
+  atomicMax(reinterpret_cast<int*>(addr), __float_as_int(v));
+}
+
+// ---------------------------------------------------------------------------
+// the transform kernel (one pass)
+// ---------------------------------------------------------------------------
+template <class K, bool FT>
+__global__ void __launch_bounds__(K::NT) tf_pass_kernel(const PassArgs<typename K::real> A) {
+  using R = typename K::real;
+  using c = typename K::c;
+  constexpr int E = K::E, P = K::P, S = K::S;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  c* sm = reinterpret_cast<c*>(smem_raw);
+
+  const int tid = threadIdx.x;
+  const int slot = K::SLOT_FAST ? (tid % S) : (tid / P);
+  const int t = K::SLOT_FAST ? (tid / S) : (tid % P);
+  const Geo g = A.geo;
+  const long long stride = gridDim.x;
+
+  // checksum-group state (per thread)
+  c xs[FT ? E : 1], ys[FT ? E : 1];
+  R s1r = 0, s1i = 0, s2r = 0, s2i = 0, en = 0;
+  int bad_lo = 0x7fffffff, bad_hi = -1;
+  int gi = 0;                     // transaction index inside the group
+  long long g_unit0 = blockIdx.x;
+  long long groups = 0;
+  float max_ratio = 0.f;
+  if constexpr (FT) {
+#pragma unroll
+    for (int i = 0; i < E; ++i) { xs[i] = mk<c>(0, 0); ys[i] = mk<c>(0, 0); }
+  }
+
+  for (long long unit = blockIdx.x; unit < A.num_units; unit += stride) {
+    const long long sig = signal_of<K>(g, unit, slot);
+    const bool valid = sig >= 0;
+    c a[E];
+    // ---- load (coalesced across the threads of a slot, or across slots)
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      c v = mk<c>(0, 0);
+      if (valid) v = A.in[in_off<K>(g, sig, t + i * P)];
+      a[i] = A.conj_in ? cconj(v) : v;
+    }
+    // ---- input side of the checksums
+    c pin = mk<c>(0, 0);
+    if constexpr (FT) {
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        xs[i] = cadd(xs[i], a[i]);
+        cmac(pin, ldg(A.vv + t + i * P), a[i]);
+        en += a[i].x * a[i].x + a[i].y * a[i].y;
+      }
+    }
+    // ---- injection context (armed one-shot site)
+    InjCtx ic{false, 0, 0, 0, 0};
+    if (A.inj.active && valid && A.inj.pass == A.pass_id && A.inj.signal == sig) {
+      ic.on = true;
+      ic.stage = A.inj.stage;
+      ic.pos = A.inj.pos;
+      ic.comp = A.inj.comp;
+      ic.bit = A.inj.bit;
+    }
+    // ---- the radix passes
+    Passes<K, 0>::run(a, sm, A.tw, slot, t, ic);
+    // ---- inter-pass twiddle (four-step, first pass), output side of checksums
+    c pout = mk<c>(0, 0);
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int pos = t + i * P;
+      if constexpr (K::KIND == KIND_COL) {
+        const c w = colTwiddle<K>(g, A.tlo, A.thi, valid ? sig : 0, pos);
+        if constexpr (FT) ys[i] = cadd(ys[i], a[i]);
+        a[i] = cmul(a[i], w);
+        if constexpr (FT) cmac(pout, cmul(ldg(A.ev + pos), cconj(w)), a[i]);
+      } else {
+        if constexpr (FT) {
+          ys[i] = cadd(ys[i], a[i]);
+          cmac(pout, ldg(A.ev + pos), a[i]);
+        }
+      }
+    }
+    // ---- store
+    if constexpr (K::KIND == KIND_ROW) {
+      // transposed store: rows r0..r0+S-1 are contiguous in the output for a
+      // fixed k2, so go through shared memory and store slot-fast
+#pragma unroll
+      for (int i = 0; i < E; ++i) sm[slot * K::NS + ((t + i * P) ^ (slot & ((1 << K::B) - 1)))] = a[i];
+      __syncthreads();
+      const int s2 = tid % S, t2 = tid / S;
+      const long long sig2 = signal_of<K>(g, unit, s2);
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const int pos = t2 + i * P;
+        c v = sm[s2 * K::NS + (pos ^ (s2 & ((1 << K::B) - 1)))];
+        if (A.conj_out) v = cconj(v);
+        v = cscale(v, A.out_scale);
+        A.out[out_off<K>(g, sig2, pos)] = v;
+      }
+      __syncthreads();
+    } else {
+      if (valid) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+          c v = a[i];
+          if (A.conj_out) v = cconj(v);
+          v = cscale(v, A.out_scale);
+          A.out[out_off<K>(g, sig, t + i * P)] = v;
+        }
+      }
+    }
+    // ---- per-transaction checksum residual, location encoding
+    if constexpr (FT) {
+      const R rr = pout.x - pin.x, ri = pout.y - pin.y;
+      if (!(isfinite(rr) && isfinite(ri))) {
+        bad_lo = min(bad_lo, gi);
+        bad_hi = max(bad_hi, gi);
+      }
+      s1r += rr;
+      s1i += ri;
+      s2r += (R)(gi + 1) * rr;
+      s2i += (R)(gi + 1) * ri;
+    }
+    ++gi;
+    const bool group_end = (gi == A.T) || (unit + stride >= A.num_units);
+    if constexpr (FT) {
+      if (group_end) {
+        // ---- reduce the group over the threads of each slot
+        __syncthreads();  // the exchange buffer is free now
+        double* red = reinterpret_cast<double*>(smem_raw);
+        int* flag = reinterpret_cast<int*>(smem_raw + (size_t)Seg<K>::COUNT * 8 * sizeof(double));
+        R v0 = seg_reduce_sum<K>(s1r), v1 = seg_reduce_sum<K>(s1i);
+        R v2 = seg_reduce_sum<K>(s2r), v3 = seg_reduce_sum<K>(s2i);
+        R v4 = seg_reduce_sum<K>(en);
+        int blo = seg_reduce_min<K>(bad_lo), bhi = seg_reduce_max<K>(bad_hi);
+        int seg;
+        if (seg_leader<K>(tid, seg)) {
+          double* d = red + seg * 8;
+          d[0] = (double)v0; d[1] = (double)v1; d[2] = (double)v2; d[3] = (double)v3; d[4] = (double)v4;
+          d[5] = (double)blo; d[6] = (double)bhi;
+        }
+        __syncthreads();
+        if (tid < S) {
+          double S1r = 0, S1i = 0, S2r = 0, S2i = 0, EN = 0;
+          int lo = 0x7fffffff, hi = -1;
+          for_slot_segments<K>(tid, [&](int sgi) {
+            const double* d = red + sgi * 8;
+            S1r += d[0]; S1i += d[1]; S2r += d[2]; S2i += d[3]; EN += d[4];
+            lo = min(lo, (int)d[5]); hi = max(hi, (int)d[6]);
+          });
+          const double tau = A.tau_coef * sqrt((double)K::NS * EN);
+          const double mag = sqrt(S1r * S1r + S1i * S1i);
+          const bool finite = isfinite(S1r) && isfinite(S1i) && isfinite(EN);
+          int rec = -1;
+          // a slot with no valid signal in this group has EN == 0 and S1 == 0
+          if (finite && mag <= tau) {
+            if (tau > 0) max_ratio = fmaxf(max_ratio, (float)(mag / tau));
+          } else {
+            int located = -1;
+            if (hi >= 0) {
+              located = (lo == hi) ? lo : -2;   // non-finite residuals: direct location
+            } else if (finite) {
+              const double den = S1r * S1r + S1i * S1i;
+              const double qr = (S2r * S1r + S2i * S1i) / den, qi = (S2i * S1r - S2r * S1i) / den;
+              const double kk = floor(qr + 0.5);
+              if (isfinite(qr) && isfinite(qi) && kk >= 1 && kk <= gi &&
+                  sqrt((qr - kk) * (qr - kk) + qi * qi) < 0.25)
+                located = (int)kk - 1;
+            }
+            atomicAdd(&A.fts->detected, 1ull);
+            unsigned long long r = atomicAdd(&A.fts->num_records, 1ull);
+            if (r < (unsigned long long)MAX_RECORDS) {
+              FtRecord& R0 = A.fts->rec[r];
+              R0.pass_id = A.pass_id;
+              R0.slot = tid;
+              R0.count = gi;
+              R0.located = located;
+              R0.unit0 = g_unit0;
+              R0.unit_stride = stride;
+              R0.transform_base = A.transform_base;
+              R0.s1r = S1r; R0.s1i = S1i; R0.s2r = S2r; R0.s2i = S2i;
+              R0.tau = tau;
+              R0.energy = EN;
+              R0.result = FT_RES_PENDING;
+              R0.signal = -1;
+              rec = (int)r;
+            } else {
+              atomicAdd(&A.fts->dropped, 1ull);
+            }
+          }
+          flag[tid] = rec;
+        }
+        __syncthreads();
+        const int myrec = flag[slot];
+        if (myrec >= 0) {
+          // right-side sums of this slot -> the record, for delayed correction
+          c* xr = reinterpret_cast<c*>(A.rec_sums) + (size_t)myrec * 2 * A.rec_stride;
+          c* yr = xr + A.rec_stride;
+#pragma unroll
+          for (int i = 0; i < E; ++i) { xr[t + i * P] = xs[i]; yr[t + i * P] = ys[i]; }
+        }
+        __syncthreads();
+        ++groups;
+#pragma unroll
+        for (int i = 0; i < E; ++i) { xs[i] = mk<c>(0, 0); ys[i] = mk<c>(0, 0); }
+        s1r = s1i = s2r = s2i = en = 0;
+        bad_lo = 0x7fffffff;
+        bad_hi = -1;
+      }
+    }
+    if (group_end) {
+      gi = 0;
+      g_unit0 = unit + stride;
+    }
+  }
+  if constexpr (FT) {
+    if (tid == 0 && groups > 0) atomicAdd(&A.fts->groups, (unsigned long long)(groups * S));
+    if (tid < S && max_ratio > 0.f) atomic_max_nonneg(&A.fts->max_clean_ratio, max_ratio);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// correction kernel: one block per record of this pass (Sec. 4.1.2)
+//   located signal k:  Delta = y_bar - W x_bar,  y_k <- y_k - Delta, re-check;
+//   otherwise (or if that fails) recompute y_k from its untouched input;
+//   ambiguous location: per-signal re-check of the group from HBM.
+// ---------------------------------------------------------------------------
+// load signal `sig` of this pass's input into the home registers (slot-0
+// layout; every slot of the block computes the same thing)
+template <class K>
+__device__ __forceinline__ void load_input(const PassArgs<typename K::real>& A, long long sig, int t,
+                                           typename K::c (&a)[K::E]) {
+#pragma unroll
+  for (int i = 0; i < K::E; ++i) {
+    auto v = A.in[in_off<K>(A.geo, sig, t + i * K::P)];
+    a[i] = A.conj_in ? cconj(v) : v;
+  }
+}
+
+// stored output of signal `sig`, mapped back to the internal (pre-store,
+// for KIND_COL pre-twiddle) domain
+template <class K>
+__device__ __forceinline__ void load_output_internal(const PassArgs<typename K::real>& A, long long sig, int t,
+                                                     typename K::c (&a)[K::E]) {
+  using R = typename K::real;
+#pragma unroll
+  for (int i = 0; i < K::E; ++i) {
+    const int pos = t + i * K::P;
+    auto v = A.out[out_off<K>(A.geo, sig, pos)];
+    v = cscale(v, (R)1 / A.out_scale);
+    if (A.conj_out) v = cconj(v);
+    if constexpr (K::KIND == KIND_COL) v = cmul(v, cconj(colTwiddle<K>(A.geo, A.tlo, A.thi, sig, pos)));
+    a[i] = v;
+  }
+}
+
+template <class K>
+__device__ __forceinline__ void store_output_internal(const PassArgs<typename K::real>& A, long long sig, int t,
+                                                      const typename K::c (&a)[K::E]) {
+#pragma unroll
+  for (int i = 0; i < K::E; ++i) {
+    const int pos = t + i * K::P;
+    auto v = a[i];
+    if constexpr (K::KIND == KIND_COL) v = cmul(v, colTwiddle<K>(A.geo, A.tlo, A.thi, sig, pos));
+    if (A.conj_out) v = cconj(v);
+    v = cscale(v, A.out_scale);
+    A.out[out_off<K>(A.geo, sig, pos)] = v;
+  }
+}
+
+// block-wide sum of slot-0 contributions, in double
+template <class K> __device__ __forceinline__ void block_sum3(double* red, double& a, double& b, double& c3) {
+  const int tid = threadIdx.x;
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    c3 += __shfl_xor_sync(0xffffffffu, c3, o);
+  }
+  __syncthreads();
+  if ((tid & 31) == 0) { red[(tid >> 5) * 3 + 0] = a; red[(tid >> 5) * 3 + 1] = b; red[(tid >> 5) * 3 + 2] = c3; }
+  __syncthreads();
+  a = b = c3 = 0;
+  for (int w = 0; w < K::NT / 32; ++w) { a += red[w * 3]; b += red[w * 3 + 1]; c3 += red[w * 3 + 2]; }
+  __syncthreads();
+}
+
+// residual r = e . y - v . x and energy of one signal (slot 0's threads)
+template <class K>
+__device__ __forceinline__ void residual(const PassArgs<typename K::real>& A, double* red, int slot, int t,
+                                         const typename K::c (&x)[K::E], const typename K::c (&y)[K::E],
+                                         double& rr, double& ri, double& en) {
+  double a = 0, b = 0, e2 = 0;
+  if (slot == 0) {
+#pragma unroll
+    for (int i = 0; i < K::E; ++i) {
+      const int pos = t + i * K::P;
+      auto ev = ldg(A.ev + pos), vv = ldg(A.vv + pos);
+      double yr = y[i].x, yi = y[i].y, xr = x[i].x, xi = x[i].y;
+      a += (double)ev.x * yr - (double)ev.y * yi - ((double)vv.x * xr - (double)vv.y * xi);
+      b += (double)ev.x * yi + (double)ev.y * yr - ((double)vv.x * xi + (double)vv.y * xr);
+      e2 += xr * xr + xi * xi;
+    }
+  }
+  block_sum3<K>(red, a, b, e2);
+  rr = a; ri = b; en = e2;
+}
+
+// does signal `sig` pass its own checksum test (from HBM, float64)?
+template <class K>
+__device__ __forceinline__ bool signal_passes(const PassArgs<typename K::real>& A, double* red, int slot, int t,
+                                              long long sig) {
+  typename K::c x[K::E], y[K::E];
+  load_input<K>(A, sig, t, x);
+  load_output_internal<K>(A, sig, t, y);
+  double rr, ri, en;
+  residual<K>(A, red, slot, t, x, y, rr, ri, en);
+  const double m = sqrt(rr * rr + ri * ri);
+  return m <= A.tau_coef * sqrt((double)K::NS * en);  // false for NaN
+}
+
+template <class K>
+__global__ void __launch_bounds__(K::NT) tf_fix_kernel(const PassArgs<typename K::real> A) {
+  using c = typename K::c;
+  constexpr int E = K::E, P = K::P, S = K::S;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  c* sm = reinterpret_cast<c*>(smem_raw);
+  __shared__ double red[3 * 32];
+
+  const unsigned long long nrec = A.fts->num_records;
+  const int tid = threadIdx.x;
+  const int slot = K::SLOT_FAST ? (tid % S) : (tid / P);
+  const int t = K::SLOT_FAST ? (tid / S) : (tid % P);
+
+  for (unsigned long long r = blockIdx.x; r < nrec && r < (unsigned long long)MAX_RECORDS; r += gridDim.x) {
+    FtRecord& rec = A.fts->rec[r];
+    // uniform across the block: records of other passes, or already handled
+    if (rec.pass_id != A.pass_id || rec.result != FT_RES_PENDING) continue;
+    auto sig_of = [&](int k) { return signal_of<K>(A.geo, rec.unit0 + (long long)k * rec.unit_stride, rec.slot); };
+
+    int k = rec.located;
+    if (k == -1) {
+      // ambiguous location: re-check every signal of the group on its own
+      int found = -1, nbad = 0;
+      for (int kk = 0; kk < rec.count; ++kk) {
+        const long long s = sig_of(kk);
+        if (s < 0) continue;
+        if (!signal_passes<K>(A, red, slot, t, s)) { ++nbad; found = kk; }
+      }
+      if (nbad == 0) {
+        if (tid == 0) rec.result = FT_RES_CLEAR;
+        continue;
+      }
+      k = (nbad == 1) ? found : -2;
+    }
+    const long long sk = (k >= 0 && k < rec.count) ? sig_of(k) : -1;
+    if (sk < 0) {
+      if (tid == 0) { rec.result = FT_RES_UNCORRECTABLE; atomicAdd(&A.fts->uncorrectable, 1ull); }
+      continue;
+    }
+    if (tid == 0) { rec.signal = sk; atomicAdd(&A.fts->located, 1ull); }
+    if (A.ft != FT_CORRECT) {
+      if (tid == 0) rec.result = FT_RES_LOCATED;
+      continue;
+    }
+    c x[E], y_old[E];
+    load_input<K>(A, sk, t, x);
+    load_output_internal<K>(A, sk, t, y_old);
+    double r_old_r, r_old_i, en;
+    residual<K>(A, red, slot, t, x, y_old, r_old_r, r_old_i, en);
+    const double tau_k = A.tau_coef * sqrt((double)K::NS * en);
+
+    // (1) the paper's correction from the right-side sums:
+    //     Delta = y_bar - W x_bar, y_k <- y_k - Delta
+    int how = 0;
+    {
+      const c* xr = reinterpret_cast<const c*>(A.rec_sums) + (size_t)r * 2 * A.rec_stride;
+      const c* yr = xr + A.rec_stride;
+      c a[E];
+#pragma unroll
+      for (int i = 0; i < E; ++i) a[i] = xr[t + i * P];
+      fft_block<K>(a, sm, A.tw, slot, t);
+      c cand[E];
+      bool fin = true;
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const c d = csub(yr[t + i * P], a[i]);
+        cand[i] = csub(y_old[i], d);
+        fin = fin && isfinite(cand[i].x) && isfinite(cand[i].y);
+      }
+      fin = __syncthreads_and(fin);
+      if (fin) {
+        double rr, ri, e2;
+        residual<K>(A, red, slot, t, x, cand, rr, ri, e2);
+        if (sqrt(rr * rr + ri * ri) <= tau_k) {
+          if (slot == 0) store_output_internal<K>(A, sk, t, cand);
+          how = FT_RES_DELTA;
+        }
+      }
+    }
+    if (how == 0) {
+      // (2) recompute the signal from its untouched input
+      c a[E];
+#pragma unroll
+      for (int i = 0; i < E; ++i) a[i] = x[i];
+      fft_block<K>(a, sm, A.tw, slot, t);
+      double rr, ri, e2;
+      residual<K>(A, red, slot, t, x, a, rr, ri, e2);
+      if (sqrt(rr * rr + ri * ri) <= tau_k) {
+        if (slot == 0) store_output_internal<K>(A, sk, t, a);
+        how = FT_RES_RECOMPUTE;
+      }
+    }
+    // (3) the rest of the group must pass signal by signal: a second
+    //     corrupted signal violates the single-error model
+    bool rest_ok = true;
+    if (how != 0 && rec.located >= 0) {
+      __syncthreads();
+      for (int kk = 0; kk < rec.count; ++kk) {
+        const long long s = sig_of(kk);
+        if (kk == k || s < 0) continue;
+        if (!signal_passes<K>(A, red, slot, t, s)) rest_ok = false;
+      }
+    }
+    if (tid == 0) {
+      if (how != 0 && rest_ok) {
+        rec.result = how;
+        atomicAdd(&A.fts->corrected, 1ull);
+        if (how == FT_RES_RECOMPUTE) atomicAdd(&A.fts->recomputed, 1ull);
+      } else {
+        if (how != 0) atomicAdd(&A.fts->corrected, 1ull);
+        rec.result = FT_RES_UNCORRECTABLE;
+        atomicAdd(&A.fts->uncorrectable, 1ull);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace tf

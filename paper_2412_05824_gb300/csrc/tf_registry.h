@@ -1,0 +1,36 @@
+// Host-side registry of the compiled kernel configurations.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace tf {
+
+typedef void (*LaunchFn)(const void* args, int grid, cudaStream_t stream);
+
+struct KernelEntry {
+  int dtype;        // 0 float, 1 double
+  int kind;         // Kind
+  int ns;           // sub-transform length
+  int e;            // complex values per thread (= radix of the first passes)
+  int s;            // sub-transforms per transaction
+  int nt;           // threads per block
+  int stages;       // radix passes
+  int smem_main;    // dynamic shared memory of the transform kernel
+  int smem_fix;     // dynamic shared memory of the correction kernel
+  LaunchFn main_plain, main_ft, fix;
+  const void* fn_plain;
+  const void* fn_ft;
+  const void* fn_fix;
+};
+
+// all entries of one translation unit
+typedef const KernelEntry* (*EntryTableFn)(int* count);
+
+const KernelEntry* entries_f32_sp(int* count);
+const KernelEntry* entries_f32_col(int* count);
+const KernelEntry* entries_f32_row(int* count);
+const KernelEntry* entries_f64_sp(int* count);
+const KernelEntry* entries_f64_col(int* count);
+const KernelEntry* entries_f64_row(int* count);
+
+}  // namespace tf

@@ -1,0 +1,84 @@
+"""C-ABI library checks that need no GPU: the shared library loads, exports
+every function include/turbofft.h declares, and rejects bad arguments before
+touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2412_05824_gb300 as tfl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "turbofft.h")
+
+
+def _declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(turbofft_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not os.path.exists(tfl.LIB_PATH):
+        from paper_2412_05824_gb300 import build as b
+        b.build()
+    return tfl.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ["turbofft_plan_create", "turbofft_exec", "turbofft_inject", "turbofft_destroy",
+                     "turbofft_get_report", "turbofft_exec_host"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    for name in _declared_functions():
+        assert hasattr(L, name), name
+    assert sorted(tfl.EXPORTS) == sorted(_declared_functions())
+
+
+def test_status_strings(L):
+    for code in range(7):
+        assert L.turbofft_status_string(code).decode().startswith("TURBOFFT_")
+    assert L.turbofft_status_string(99) == b"TURBOFFT_UNKNOWN_STATUS"
+
+
+@pytest.mark.parametrize("n,batch,dtype,direction,ft", [
+    (12, 4, 0, -1, 0),          # not a power of two
+    (4, 4, 0, -1, 0),           # below the minimum length 8
+    (1 << 25, 1, 0, -1, 0),     # above the maximum length 2^24
+    (64, 0, 0, -1, 0),          # empty batch
+    (64, 1 << 30, 0, -1, 0),    # too many elements
+    (64, 4, 7, -1, 0),          # bad dtype
+    (64, 4, 0, 0, 0),           # bad direction
+    (64, 4, 0, -1, 9),          # bad ft mode
+])
+def test_plan_create_rejects_bad_arguments(L, n, batch, dtype, direction, ft):
+    h = ctypes.c_void_p(123)
+    st = L.turbofft_plan_create(n, batch, dtype, direction, ft, ctypes.byref(h))
+    assert st == tfl.INVALID_VALUE
+    assert not h.value
+
+
+def test_null_handles_are_rejected(L):
+    assert L.turbofft_exec(None, None, None, None) == tfl.INVALID_VALUE
+    assert L.turbofft_exec_host(None, None, None, None) == tfl.INVALID_VALUE
+    assert L.turbofft_inject(None, tfl.Site(0, 0, 0, 0, 0), 3) == tfl.INVALID_VALUE
+    r = tfl.Report()
+    assert L.turbofft_get_report(None, ctypes.byref(r)) == tfl.INVALID_VALUE
+    assert L.turbofft_plan_get_info(None, None) == tfl.INVALID_VALUE
+    assert L.turbofft_set_threshold_scale(None, 1.0) == tfl.INVALID_VALUE
+    assert L.turbofft_destroy(None) == tfl.SUCCESS
+    assert L.turbofft_plan_create(64, 4, 0, -1, 0, None) == tfl.INVALID_VALUE
+
+
+def test_no_gpu_reports_cuda_error_not_crash(L):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    st = L.turbofft_plan_create(64, 4, 0, -1, 0, ctypes.byref(h))
+    assert st == tfl.CUDA_ERROR and not h.value
