@@ -1,0 +1,418 @@
+#!/usr/bin/env python
+"""Benchmark of the batched C2C FFT with fused two-sided ABFT.
+
+One step = the size sweep: float32 and float64, forward and inverse, N = 2^3
+.. 2^24, each call transforming 2^28 complex elements (2 GiB complex64 /
+4 GiB complex128 in, the same out), with the whole hot path on (checksum
+encode, transform, group check, correction kernel: ft_mode CORRECT).
+Reported value: aggregate GB/s = (bytes in + bytes out) / time over the step.
+The plain sweep (ABFT off) is timed the same way for the overhead figure.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: one process per GPU under torch.distributed.run; each rank runs
+the same per-GPU workload on its own data (transforms are independent, no
+exchange), value = bytes of all ranks / max time over ranks.
+`--impl reference` times the CPU oracle on a bounded sample of the same sweep.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "batched C2C FFT GB/s & GFLOP/s (5N·log2N) vs HBM roofline; ABFT overhead %"
+ELEMENTS = 1 << 28
+SIZES = [1 << k for k in range(3, 25)]
+DTYPES = [("float32", 8), ("float64", 16)]
+DIRECTIONS = ["forward", "inverse"]
+WORKLOAD = ("size sweep: f32+f64, forward+inverse, N=2^3..2^24, 2^28 complex elements per call, "
+            "two-sided ABFT on (correct mode)")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sizes", default="", help="comma list of log2 N (default: the full sweep)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def configs(args):
+    ks = [int(v) for v in args.sizes.split(",")] if args.sizes else [int(math.log2(n)) for n in SIZES]
+    return [(dt, eb, d, 1 << k) for dt, eb in DTYPES for d in DIRECTIONS for k in ks]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        load = [v for v in sm if v > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def src_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2412_05824_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(key):
+    """Traffic per launch from a committed ncu summary, if it was taken on
+    the current kernel sources."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    ent = t.get(key)
+    if ent and ent.get("src_hash") == src_hash():
+        return ent.get("traffic_bytes_per_launch")
+    return None
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle on a bounded sample (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_sample(args, sample_elems=1 << 22):
+    import numpy as np
+
+    import oracle
+    import synth_signals as ss
+
+    total_bytes = 0.0
+    total_s = 0.0
+    for dt, eb, d, n in configs(args):
+        batch = max(1, sample_elems // n)
+        x = ss.uniform_complex(2, batch, n, np.float32 if dt == "float32" else np.float64)
+        t0 = time.perf_counter()
+        oracle.fft(x, inverse=(d == "inverse"))
+        total_s += time.perf_counter() - t0
+        total_bytes += 2.0 * batch * n * eb
+    return total_bytes / total_s / 1e9, total_s, oracle.last_threads()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.lib()
+    for _ in range(args.warmup):
+        oracle_sample(args, 1 << 18)
+    vals, secs = [], []
+    threads = 1
+    for _ in range(args.steps):
+        v, s, threads = oracle_sample(args, 1 << 20)
+        vals.append(v)
+        secs.append(s)
+    value = statistics.mean(vals)
+    sample = ("oracle (float64 radix-2, OpenMP over the batch) on 2^20 elements per sweep "
+              "configuration instead of 2^28; GB/s by the same byte formula")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * statistics.mean(secs), 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "elements_per_call": ELEMENTS, "parallelism": "replicas"},
+            "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our implementation
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2412_05824_gb300 as tfl
+    import synth_signals as ss
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfgs = configs(args)
+    peaks, peak_src = measured_peaks()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # inputs resident in HBM (seeded, per rank), one buffer per dtype
+    bufs = {}
+    for dt, eb in DTYPES:
+        x = ss.uniform_complex_torch(2 + 1000 * rank, 1, ELEMENTS, dt, device=dev)
+        bufs[dt] = (x, torch.empty_like(x))
+    workspace = torch.empty(ELEMENTS, dtype=torch.complex128, device=dev)  # two-pass intermediate
+
+    def make_plans(ft):
+        plans = {}
+        for dt, eb, d, n in cfgs:
+            p = tfl.Plan(n, ELEMENTS // n, "complex64" if dt == "float32" else "complex128", d, ft)
+            p.set_workspace(workspace)
+            plans[(dt, d, n)] = p
+        return plans
+
+    plans_ft = make_plans("correct")
+    plans_plain = make_plans("off")
+    stream = torch.cuda.current_stream(dev)
+
+    def step(plans, record=None):
+        evs = []
+        for dt, eb, d, n in cfgs:
+            x, y = bufs[dt]
+            p = plans[(dt, d, n)]
+            if record is not None:
+                e = torch.cuda.Event(enable_timing=True)
+                e.record(stream)
+                evs.append(e)
+            st = p.exec_ptr(x.data_ptr(), y.data_ptr(), stream.cuda_stream)
+            if st != tfl.SUCCESS:
+                raise RuntimeError("exec failed: %d" % st)
+        if record is not None:
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(stream)
+            evs.append(e)
+            record.append(evs)
+
+    step_bytes = sum(2.0 * ELEMENTS * eb for dt, eb, d, n in cfgs)
+
+    def timed(plans, sampler=None):
+        for _ in range(args.warmup):
+            step(plans)
+        barrier()
+        rec = []
+        if sampler:
+            sampler.start()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            step(plans, rec)
+        t1.record(stream)
+        barrier()
+        clocks = sampler.stop() if sampler else None
+        ms = t0.elapsed_time(t1)
+        per_cfg = [statistics.mean(r[i].elapsed_time(r[i + 1]) for r in rec) for i in range(len(cfgs))]
+        return ms, per_cfg, clocks
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    ms_ft, per_ft, clocks = timed(plans_ft, sampler)
+    ms_plain, per_plain, _ = timed(plans_plain)
+    # fault-tolerance outcome of the last exec of every plan: a clean run
+    fa = sum(plans_ft[(dt, d, n)].report()["detected"] for dt, eb, d, n in cfgs)
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ms_ft = max_over_ranks(ms_ft)
+    ms_plain = max_over_ranks(ms_plain)
+    value = world * step_bytes * args.steps / (ms_ft * 1e-3) / 1e9
+    value_plain = world * step_bytes * args.steps / (ms_plain * 1e-3) / 1e9
+
+    # dominant kernel: the configuration with the largest share of the step,
+    # timed kernel by kernel with events on the exec's stream
+    i_dom = max(range(len(cfgs)), key=lambda i: per_ft[i])
+    dt, eb, d, n = cfgs[i_dom]
+    p = plans_ft[(dt, d, n)]
+    p.set_profiling(True)
+    x, y = bufs[dt]
+    reps = 5
+    kt = []
+    for _ in range(reps):
+        p.exec_ptr(x.data_ptr(), y.data_ptr(), stream.cuda_stream)
+        kt.append(p.kernel_times())
+    p.set_profiling(False)
+    info = p.info()
+    mains = {}
+    for run in kt:
+        for (ps, corr, msk) in run:
+            if not corr:
+                mains.setdefault(ps, []).append(msk)
+    pass_dom = max(mains, key=lambda k: statistics.mean(mains[k]))
+    kms = statistics.mean(mains[pass_dom])
+    fix_ms = statistics.mean([msk for run in kt for (ps, corr, msk) in run if corr] or [0.0])
+    bytes_launch = 2.0 * ELEMENTS * eb
+    ns_dom = info["sub_n"][pass_dom]
+    flops_launch = 5.0 * ELEMENTS * math.log2(ns_dom)
+    kname = "%s_%s_pass%d_n%d_ft" % (dt, ["sp", "col", "row"][0 if info["num_passes"] == 1 else 1 + pass_dom],
+                                     pass_dom, ns_dom)
+    if dt == "float32":
+        ach = bytes_launch / (kms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(ach / peaks["hbm_gbs"], 4), "traffic": ncu_traffic(kname),
+                "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        peak_tf = 1.25  # FP64 nominal of GB300 (profiling recipe), 2 flops per DFMA
+        ach = flops_launch / (kms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": round(ach, 4), "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": round(ach / peak_tf, 4), "traffic": ncu_traffic(kname),
+                "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe unit counts); DFMA microbenchmark measured 0.99",
+                "hbm_gbs_achieved": round(bytes_launch / (kms * 1e-3) / 1e9, 1)}
+    roof.update({"kernel": kname, "config": {"dtype": dt, "direction": d, "n": n, "batch": ELEMENTS // n},
+                 "kernel_ms": round(kms, 4), "correction_kernel_ms": round(fix_ms, 4),
+                 "algorithmic_bytes_per_launch": bytes_launch, "algorithmic_flops_per_launch": flops_launch})
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        host = {}
+        for dt2, eb2 in DTYPES:
+            hx = bufs[dt2][0].cpu().pin_memory()
+            host[dt2] = (hx, torch.empty_like(hx).pin_memory())
+        for _ in range(1):
+            for dt2, eb2, d2, n2 in cfgs:
+                hx, hy = host[dt2]
+                plans_ft[(dt2, d2, n2)].exec_host(hx, hy)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for dt2, eb2, d2, n2 in cfgs:
+                hx, hy = host[dt2]
+                plans_ft[(dt2, d2, n2)].exec_host(hx, hy)
+        barrier()
+        el = max_over_ranks(time.perf_counter() - t0)
+        h2d = sum(ELEMENTS * eb2 for dt2, eb2, d2, n2 in cfgs)
+        e2e = {"value": round(world * step_bytes * args.steps / el / 1e9, 2), "unit": "GB/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
+               "note": "turbofft_exec_host: pinned host in/out, H2D + transform + D2H pipelined in chunks"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, s, th = oracle_sample(args, 1 << 21)
+        cpu = {"value": round(v, 4), "unit": "GB/s", "cores": th, "kind": "oracle",
+               "sample": "oracle (float64 radix-2, OpenMP) on 2^21 elements per sweep configuration "
+                         "(%.1f s of CPU work); GB/s by the same byte formula" % s}
+
+    launches_per_step = 0
+    for dt2, eb2, d2, n2 in cfgs:
+        launches_per_step += plans_ft[(dt2, d2, n2)].info()["num_passes"] * 2
+    sweep = []
+    for i, (dt2, eb2, d2, n2) in enumerate(cfgs):
+        b = 2.0 * ELEMENTS * eb2
+        sweep.append([dt2[5:], d2[:3], int(math.log2(n2)), round(b / (per_ft[i] * 1e-3) / 1e9, 1),
+                      round(b / (per_plain[i] * 1e-3) / 1e9, 1),
+                      round(5.0 * ELEMENTS * math.log2(n2) / (per_ft[i] * 1e-3) / 1e9, 1)])
+    per_dtype = {}
+    for dt2, eb2 in DTYPES:
+        idx = [i for i, c in enumerate(cfgs) if c[0] == dt2]
+        if idx:
+            b = sum(2.0 * ELEMENTS * eb2 for _ in idx)
+            per_dtype[dt2] = {"ft_gbs": round(b / (sum(per_ft[i] for i in idx) * 1e-3) / 1e9, 1),
+                              "plain_gbs": round(b / (sum(per_plain[i] for i in idx) * 1e-3) / 1e9, 1)}
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_ft / args.steps, 3),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "elements_per_call": ELEMENTS,
+                           "sizes": "2^%d..2^%d" % (int(math.log2(cfgs[0][3])), int(math.log2(cfgs[-1][3]))),
+                           "ft_mode": "correct", "l2": "inputs 2-4 GiB per call, larger than the 129 MB L2",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches_per_step * args.steps,
+                "clocks": clocks,
+                "plain_value": round(value_plain, 2),
+                "abft_overhead_pct": round(100.0 * (ms_ft / ms_plain - 1.0), 2),
+                "false_alarms_last_step": fa,
+                "per_dtype": per_dtype,
+                "sweep_columns": ["dtype", "dir", "log2N", "ft_GBs", "plain_GBs", "ft_GFLOPs"],
+                "sweep": sweep}
+        print(json.dumps(line), flush=True)
+    for pl in list(plans_ft.values()) + list(plans_plain.values()):
+        pl.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -7,7 +7,7 @@
  *       forward  y_j = sum_n x_n exp(-2 pi i j n / N)
  *       inverse  x_j = (1/N) sum_n y_n exp(+2 pi i j n / N)
  *     computed as a Stockham FFT (Sec. 3.2), in one pass over HBM for
- *     N <= 2^14 (float32) / 2^13 (float64) and in two passes (four-step,
+ *     N <= 2^13 (float32) / 2^12 (float64) and in two passes (four-step,
  *     N = N1 * N2, the kernel-level tiling of Sec. 3.1) up to N = 2^24.
  *   - Fault tolerance: the two-sided checksum of Sec. 4.1 (Eq. 4-5) fused
  *     into the transform kernels (Sec. 4.2.2), amortised over several
@@ -19,8 +19,10 @@
  * Conventions for every entry point
  *   - No call allocates or frees caller memory.  A plan owns every device
  *     and pinned-host buffer it allocates (tables, the intermediate buffer of
- *     two-pass plans, the fault-tolerance report and correction records) and
- *     frees them in turbofft_destroy.
+ *     two-pass plans unless the caller supplies one with
+ *     turbofft_set_workspace, the fault-tolerance report and correction
+ *     records) and frees them in turbofft_destroy.  turbofft_exec_host keeps
+ *     a per-device staging area (see there).
  *   - Data layout: `batch` transforms of `n` interleaved complex values
  *     (re, im), contiguous, transform b at element offset b * n.  Element
  *     type is float (TURBOFFT_C2C_F32, 8 bytes per value) or double
@@ -36,6 +38,7 @@
 #ifndef TURBOFFT_H
 #define TURBOFFT_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -69,7 +72,12 @@ typedef enum {
 typedef enum {
   TURBOFFT_FT_OFF = 0,            /* plain FFT, no checksums */
   TURBOFFT_FT_DETECT = 1,         /* checksums fused; detect and locate, report only */
-  TURBOFFT_FT_CORRECT = 2         /* detect, locate and correct in place (Sec. 4.1.2) */
+  TURBOFFT_FT_CORRECT = 2,        /* detect, locate and correct in place (Sec. 4.1.2) */
+  TURBOFFT_FT_CORRECT_REGISTERS = 3 /* CORRECT, with the right-side sums accumulated in
+                                       registers during the transform (the thread-level
+                                       accumulation of Sec. 4.3) instead of formed from the
+                                       untouched input and the stored output when a group
+                                       fails its check; same results, more registers */
 } turbofft_ft_mode;
 
 typedef struct turbofft_plan turbofft_plan;
@@ -125,8 +133,16 @@ typedef struct {
   int32_t group_transactions; /* transactions of one thread block per checksum group */
   int32_t grid[2];          /* persistent thread blocks launched per pass */
   int32_t block[2];         /* threads per block per pass */
-  int64_t workspace_bytes;  /* device memory the plan owns */
+  int64_t workspace_bytes;  /* device memory the plan owns or will allocate */
+  int64_t scratch_bytes;    /* intermediate buffer of a two-pass plan (0 for one pass) */
 } turbofft_plan_info;
+
+/* Duration of one kernel of the last exec (turbofft_set_profiling). */
+typedef struct {
+  int32_t pass;             /* kernel pass */
+  int32_t is_correction;    /* 0 = transform kernel, 1 = correction kernel */
+  double ms;                /* CUDA-event time on the exec's stream */
+} turbofft_kernel_time;
 
 /*
  * Create a plan on the current CUDA device.
@@ -161,11 +177,14 @@ turbofft_status turbofft_exec(turbofft_plan *plan, const void *in, void *out,
 /*
  * Same transform with HOST buffers: copies `host_in` to the device, runs
  * the transform and copies the result to `host_out`, pipelined in chunks of
- * the batch over two internal streams ordered after `stream`, and returns
- * when `host_out` is complete.  Host buffers should be pinned
- * (cudaHostAlloc / cudaHostRegister) for full bandwidth; pageable memory
- * works but is slower.  The plan allocates its device staging buffers on
- * the first call and keeps them until destroy.
+ * the batch over three internal streams (copy in, transform, copy out)
+ * ordered after `stream`, and returns when `host_out` is complete.  Host
+ * buffers should be pinned (cudaHostAlloc / cudaHostRegister) for full
+ * bandwidth; pageable memory works but is slower.  The device staging (five
+ * chunk buffers of about 64 MiB, or one transform if larger, and the
+ * streams) is shared by all plans of a device, allocated by the first call
+ * and kept until the process exits; calls from several host threads on one
+ * device are serialised.
  */
 turbofft_status turbofft_exec_host(turbofft_plan *plan, const void *host_in, void *host_out,
                                    turbofft_stream stream);
@@ -194,6 +213,26 @@ turbofft_status turbofft_plan_get_info(const turbofft_plan *plan, turbofft_plan_
  * Sec. 5.3.1); the default is calibrated for zero false alarms.
  */
 turbofft_status turbofft_set_threshold_scale(turbofft_plan *plan, double factor);
+
+/*
+ * Place the intermediate buffer of a two-pass plan in caller-owned device
+ * memory (`bytes` >= info.scratch_bytes, 16-byte aligned) instead of the
+ * plan allocating it at its first exec.  Plans that never run at the same
+ * time on the GPU may share one workspace.  The caller keeps ownership and
+ * must keep it alive while the plan may run.  A one-pass plan ignores the
+ * call.  Errors: INVALID_VALUE (NULL, too small, misaligned).
+ */
+turbofft_status turbofft_set_workspace(turbofft_plan *plan, void *workspace, size_t bytes);
+
+/*
+ * Record a CUDA event pair around every kernel of each following exec (on
+ * the exec's stream) when enable != 0.  turbofft_get_kernel_times waits for
+ * the last exec and returns up to `capacity` durations in launch order;
+ * *count receives how many were written.
+ */
+turbofft_status turbofft_set_profiling(turbofft_plan *plan, int enable);
+turbofft_status turbofft_get_kernel_times(turbofft_plan *plan, turbofft_kernel_time *out,
+                                          int capacity, int *count);
 
 /* Free everything the plan owns.  NULL is a no-op.  Waits for the plan's
  * outstanding work first. */

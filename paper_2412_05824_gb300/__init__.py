@@ -35,11 +35,13 @@ INVERSE_UNSCALED = 2
 FT_OFF = 0
 FT_DETECT = 1
 FT_CORRECT = 2
+FT_CORRECT_REGISTERS = 3
 
 _DIRS = {"forward": FORWARD, "inverse": INVERSE, "inverse_unscaled": INVERSE_UNSCALED,
          FORWARD: FORWARD, INVERSE: INVERSE, INVERSE_UNSCALED: INVERSE_UNSCALED}
-_FT = {"off": FT_OFF, "detect": FT_DETECT, "correct": FT_CORRECT, None: FT_OFF, False: FT_OFF,
-       FT_OFF: FT_OFF, FT_DETECT: FT_DETECT, FT_CORRECT: FT_CORRECT}
+_FT = {"off": FT_OFF, "detect": FT_DETECT, "correct": FT_CORRECT, "correct_registers": FT_CORRECT_REGISTERS,
+       None: FT_OFF, False: FT_OFF, FT_OFF: FT_OFF, FT_DETECT: FT_DETECT, FT_CORRECT: FT_CORRECT,
+       FT_CORRECT_REGISTERS: FT_CORRECT_REGISTERS}
 
 
 class Site(ctypes.Structure):
@@ -62,13 +64,19 @@ class PlanInfo(ctypes.Structure):
                 ("num_passes", ctypes.c_int32), ("sub_n", ctypes.c_int64 * 2),
                 ("stages", ctypes.c_int32 * 2), ("radix", ctypes.c_int32 * 2),
                 ("group_transactions", ctypes.c_int32), ("grid", ctypes.c_int32 * 2),
-                ("block", ctypes.c_int32 * 2), ("workspace_bytes", ctypes.c_int64)]
+                ("block", ctypes.c_int32 * 2), ("workspace_bytes", ctypes.c_int64),
+                ("scratch_bytes", ctypes.c_int64)]
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("pass_", ctypes.c_int32), ("is_correction", ctypes.c_int32), ("ms", ctypes.c_double)]
 
 
 EXPORTS = [
     "turbofft_plan_create", "turbofft_exec", "turbofft_exec_host", "turbofft_inject",
     "turbofft_get_report", "turbofft_plan_get_info", "turbofft_set_threshold_scale",
     "turbofft_destroy", "turbofft_status_string", "turbofft_last_error",
+    "turbofft_set_workspace", "turbofft_set_profiling", "turbofft_get_kernel_times",
 ]
 
 _lib = None
@@ -91,6 +99,9 @@ def lib() -> ctypes.CDLL:
     L.turbofft_plan_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
     L.turbofft_set_threshold_scale.argtypes = [vp, ctypes.c_double]
     L.turbofft_destroy.argtypes = [vp]
+    L.turbofft_set_workspace.argtypes = [vp, vp, ctypes.c_size_t]
+    L.turbofft_set_profiling.argtypes = [vp, i32]
+    L.turbofft_get_kernel_times.argtypes = [vp, ctypes.POINTER(KernelTime), i32, ctypes.POINTER(i32)]
     L.turbofft_status_string.argtypes = [i32]
     L.turbofft_status_string.restype = ctypes.c_char_p
     L.turbofft_last_error.argtypes = [vp]
@@ -194,6 +205,23 @@ class Plan:
             v = getattr(i, name)
             d[name] = list(v) if hasattr(v, "__len__") else v
         return d
+
+    def set_workspace(self, buf):
+        """Use the CUDA tensor `buf` (kept alive by the plan object) as the
+        intermediate buffer of a two-pass plan."""
+        self._workspace = buf
+        _check(lib().turbofft_set_workspace(self._h, buf.data_ptr(), buf.numel() * buf.element_size()),
+               "turbofft_set_workspace")
+
+    def set_profiling(self, enable: bool = True):
+        _check(lib().turbofft_set_profiling(self._h, 1 if enable else 0), "turbofft_set_profiling")
+
+    def kernel_times(self) -> list:
+        """[(pass, is_correction, ms)] of the last exec (profiling on)."""
+        buf = (KernelTime * 8)()
+        cnt = ctypes.c_int()
+        _check(lib().turbofft_get_kernel_times(self._h, buf, 8, ctypes.byref(cnt)), "turbofft_get_kernel_times", self._h)
+        return [(buf[i].pass_, buf[i].is_correction, buf[i].ms) for i in range(cnt.value)]
 
     def set_threshold_scale(self, factor: float):
         _check(lib().turbofft_set_threshold_scale(self._h, float(factor)), "turbofft_set_threshold_scale")

@@ -162,7 +162,9 @@ struct turbofft_plan {
   PassPlan pass[2];
   void* d_tlo = nullptr;
   void* d_thi = nullptr;
-  void* d_scratch = nullptr;
+  void* d_scratch = nullptr;      // intermediate of two-pass plans (owned or caller's)
+  size_t scratch_bytes = 0;       // bytes a two-pass exec needs
+  bool scratch_owned = false;
   FtState* d_fts = nullptr;
   FtState* h_fts = nullptr;
   void* d_rec_sums = nullptr;
@@ -174,14 +176,12 @@ struct turbofft_plan {
   bool have_exec = false;
   std::string last_error;
   int64_t workspace_bytes = 0;
-  // exec_host staging
-  void* h_stage_in[2] = {nullptr, nullptr};
-  void* h_stage_out[2] = {nullptr, nullptr};
-  void* h_scratch = nullptr;
-  int64_t chunk = 0;
-  cudaStream_t hs[3] = {nullptr, nullptr, nullptr};
-  cudaEvent_t hev[8] = {};
   std::vector<void*> allocs;
+  // per-kernel timing (turbofft_set_profiling)
+  bool profiling = false;
+  int nprof = 0;
+  cudaEvent_t prof_ev[8][2] = {};
+  int prof_kind[8] = {};
 };
 
 namespace {
@@ -226,9 +226,12 @@ bool upload_tables(turbofft_plan* p, PassPlan& pp) {
   return upload<double>(p, &pp.d_tw, tw) && upload<double>(p, &pp.d_ev, e) && upload<double>(p, &pp.d_vv, v);
 }
 
-int occupancy_blocks(const KernelEntry* ke, bool ft) {
+// kernel variant of an ft_mode: 0 none, 1 checksums, 2 checksums + register sums
+int ft_variant(int ft_mode) { return ft_mode == TURBOFFT_FT_OFF ? 0 : (ft_mode == TURBOFFT_FT_CORRECT_REGISTERS ? 2 : 1); }
+
+int occupancy_blocks(const KernelEntry* ke, int variant) {
   int nb = 0;
-  const void* fn = ft ? ke->fn_ft : ke->fn_plain;
+  const void* fn = ke->fn_main[variant];
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, ke->nt, ke->smem_main) != cudaSuccess) {
     cudaGetLastError();
     nb = 1;
@@ -238,10 +241,10 @@ int occupancy_blocks(const KernelEntry* ke, bool ft) {
 
 bool set_smem_attrs(const KernelEntry* ke) {
   // the attribute is per function; setting it again is harmless
-  if (cudaFuncSetAttribute(ke->fn_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, ke->smem_main) != cudaSuccess)
-    return false;
-  if (cudaFuncSetAttribute(ke->fn_ft, cudaFuncAttributeMaxDynamicSharedMemorySize, ke->smem_main) != cudaSuccess)
-    return false;
+  for (int v = 0; v < 3; ++v)
+    if (cudaFuncSetAttribute(ke->fn_main[v], cudaFuncAttributeMaxDynamicSharedMemorySize, ke->smem_main) !=
+        cudaSuccess)
+      return false;
   if (cudaFuncSetAttribute(ke->fn_fix, cudaFuncAttributeMaxDynamicSharedMemorySize, ke->smem_fix) != cudaSuccess)
     return false;
   return true;
@@ -278,7 +281,7 @@ void fill_args(const turbofft_plan* p, int pi, const void* in, void* out, int64_
   A.conj_out = (inverse && last) ? 1 : 0;
   A.out_scale = (last && p->direction == TURBOFFT_INVERSE) ? (R)(1.0 / (double)p->n) : (R)1;
   A.tau_coef = pp.tau_coef * p->threshold_scale;
-  A.ft = p->ft_mode;
+  A.ft = p->ft_mode == TURBOFFT_FT_CORRECT_REGISTERS ? TURBOFFT_FT_CORRECT : p->ft_mode;
   A.T = p->T;
   A.pass_id = pi;
   A.transform_base = tbase;
@@ -299,16 +302,25 @@ turbofft_status run(turbofft_plan* p, const void* in, void* out, void* scratch, 
     long long units = units_for(p, pi, batch);
     int grid = (int)std::min<long long>(units, pp.grid);
     if (grid < 1) grid = 1;
+    auto timed = [&](int kind, auto&& launch) {
+      const bool prof = p->profiling && p->nprof < 8;
+      if (prof) cudaEventRecord(p->prof_ev[p->nprof][0], stream);
+      launch();
+      if (prof) {
+        cudaEventRecord(p->prof_ev[p->nprof][1], stream);
+        p->prof_kind[p->nprof++] = kind;
+      }
+    };
     if (p->dtype == TURBOFFT_C2C_F32) {
       tf::PassArgs<float> A;
       fill_args<float>(p, pi, pin, pout, batch, tbase, inj, A);
-      (ft ? pp.ke->main_ft : pp.ke->main_plain)(&A, grid, stream);
-      if (ft) pp.ke->fix(&A, 8, stream);
+      timed(2 * pi, [&] { pp.ke->main[ft_variant(p->ft_mode)](&A, grid, stream); });
+      if (ft) timed(2 * pi + 1, [&] { pp.ke->fix(&A, 8, stream); });
     } else {
       tf::PassArgs<double> A;
       fill_args<double>(p, pi, pin, pout, batch, tbase, inj, A);
-      (ft ? pp.ke->main_ft : pp.ke->main_plain)(&A, grid, stream);
-      if (ft) pp.ke->fix(&A, 8, stream);
+      timed(2 * pi, [&] { pp.ke->main[ft_variant(p->ft_mode)](&A, grid, stream); });
+      if (ft) timed(2 * pi + 1, [&] { pp.ke->fix(&A, 8, stream); });
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(p, e, "kernel launch");
@@ -317,6 +329,45 @@ turbofft_status run(turbofft_plan* p, const void* in, void* out, void* scratch, 
 }
 
 bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
+
+// Device staging of turbofft_exec_host, shared by all plans of a device:
+// two input and two output chunk buffers plus a chunk-sized intermediate,
+// three streams (copy in, transform, copy out) and their events.  Grown on
+// demand, kept until the process exits; one exec_host runs at a time per
+// device (the call is synchronous).
+struct HostStage {
+  std::mutex mu;
+  size_t chunk_bytes = 0;
+  void* in[2] = {nullptr, nullptr};
+  void* out[2] = {nullptr, nullptr};
+  void* scratch = nullptr;
+  cudaStream_t st[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev[8] = {};
+  bool ready = false;
+};
+HostStage g_stage[16];
+const size_t kStageChunkBytes = (size_t)64 << 20;
+
+cudaError_t stage_reserve(HostStage& hs, size_t need) {
+  cudaError_t e;
+  if (!hs.ready) {
+    for (auto& s : hs.st)
+      if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    for (auto& v : hs.ev)
+      if ((e = cudaEventCreateWithFlags(&v, cudaEventDisableTiming)) != cudaSuccess) return e;
+    hs.ready = true;
+  }
+  if (need <= hs.chunk_bytes) return cudaSuccess;
+  for (void** b : {&hs.in[0], &hs.in[1], &hs.out[0], &hs.out[1], &hs.scratch}) {
+    if (*b) cudaFree(*b);
+    *b = nullptr;
+  }
+  hs.chunk_bytes = 0;
+  for (void** b : {&hs.in[0], &hs.in[1], &hs.out[0], &hs.out[1], &hs.scratch})
+    if ((e = cudaMalloc(b, need)) != cudaSuccess) return e;
+  hs.chunk_bytes = need;
+  return cudaSuccess;
+}
 
 }  // namespace
 
@@ -349,10 +400,9 @@ turbofft_status turbofft_destroy(turbofft_plan* p) {
   for (void* a : p->allocs) cudaFree(a);
   if (p->h_fts) cudaFreeHost(p->h_fts);
   if (p->done) cudaEventDestroy(p->done);
-  for (auto& s : p->hs)
-    if (s) cudaStreamDestroy(s);
-  for (auto& e : p->hev)
-    if (e) cudaEventDestroy(e);
+  for (auto& pr : p->prof_ev)
+    for (auto& e : pr)
+      if (e) cudaEventDestroy(e);
   cudaGetLastError();
   cudaSetDevice(cur);
   delete p;
@@ -369,7 +419,8 @@ turbofft_status turbofft_plan_create(int64_t n, int64_t batch, turbofft_dtype dt
   if (dtype != TURBOFFT_C2C_F32 && dtype != TURBOFFT_C2C_F64) return TURBOFFT_INVALID_VALUE;
   if (direction != TURBOFFT_FORWARD && direction != TURBOFFT_INVERSE && direction != TURBOFFT_INVERSE_UNSCALED)
     return TURBOFFT_INVALID_VALUE;
-  if (ft_mode != TURBOFFT_FT_OFF && ft_mode != TURBOFFT_FT_DETECT && ft_mode != TURBOFFT_FT_CORRECT)
+  if (ft_mode != TURBOFFT_FT_OFF && ft_mode != TURBOFFT_FT_DETECT && ft_mode != TURBOFFT_FT_CORRECT &&
+      ft_mode != TURBOFFT_FT_CORRECT_REGISTERS)
     return TURBOFFT_INVALID_VALUE;
 
   int dev = 0;
@@ -420,7 +471,7 @@ turbofft_status turbofft_plan_create(int64_t n, int64_t batch, turbofft_dtype dt
       delete p;
       return TURBOFFT_CUDA_ERROR;
     }
-    const int occ = occupancy_blocks(pp.ke, ft_mode != TURBOFFT_FT_OFF);
+    const int occ = occupancy_blocks(pp.ke, ft_variant(ft_mode));
     pp.grid = occ * g_num_sms;
     pp.tau_coef = kGamma[dt] * kUnitRoundoff[dt] * sqrt((double)ilog2_exact(pp.ns));
     if (!upload_tables(p, pp)) {
@@ -435,7 +486,8 @@ turbofft_status turbofft_plan_create(int64_t n, int64_t batch, turbofft_dtype dt
     for (size_t j = 0; j < hi.size(); ++j) hi[j] = root(n, (int64_t)j * 4096);
     bool ok = (dt == 0) ? (upload<float>(p, &p->d_tlo, lo) && upload<float>(p, &p->d_thi, hi))
                         : (upload<double>(p, &p->d_tlo, lo) && upload<double>(p, &p->d_thi, hi));
-    if (!ok || !dev_alloc(p, &p->d_scratch, (size_t)(batch * n) * elem_bytes(dtype))) {
+    p->scratch_bytes = (size_t)(batch * n) * elem_bytes(dtype);
+    if (!ok) {
       turbofft_destroy(p);
       return TURBOFFT_ALLOC_FAILED;
     }
@@ -487,7 +539,8 @@ turbofft_status turbofft_plan_get_info(const turbofft_plan* p, turbofft_plan_inf
   }
   if (p->num_passes == 1) info->sub_n[1] = 1;
   info->group_transactions = p->T;
-  info->workspace_bytes = p->workspace_bytes;
+  info->workspace_bytes = p->workspace_bytes + (p->scratch_owned ? 0 : (int64_t)p->scratch_bytes);
+  info->scratch_bytes = (int64_t)p->scratch_bytes;
   return TURBOFFT_SUCCESS;
 }
 
@@ -540,8 +593,13 @@ turbofft_status turbofft_exec(turbofft_plan* p, const void* in, void* out, turbo
     cudaError_t e = cudaMemsetAsync(p->d_fts, 0, tf::FT_HEADER_BYTES, s);
     if (e != cudaSuccess) return cuda_fail(p, e, "report reset");
   }
+  if (p->num_passes == 2 && !p->d_scratch) {
+    if (!dev_alloc(p, &p->d_scratch, p->scratch_bytes)) return TURBOFFT_ALLOC_FAILED;
+    p->scratch_owned = true;
+  }
   tf::InjectSite inj = p->armed;
   p->armed.active = 0;
+  p->nprof = 0;
   turbofft_status st = run(p, in, out, p->d_scratch, p->batch, 0, s, inj);
   if (st != TURBOFFT_SUCCESS) return st;
   if (ft) {
@@ -556,86 +614,122 @@ turbofft_status turbofft_exec(turbofft_plan* p, const void* in, void* out, turbo
 
 turbofft_status turbofft_exec_host(turbofft_plan* p, const void* host_in, void* host_out, turbofft_stream stream) {
   if (!p || !host_in || !host_out) return TURBOFFT_INVALID_VALUE;
+  if (p->device < 0 || p->device >= 16) return TURBOFFT_UNSUPPORTED;
   const size_t eb = elem_bytes(p->dtype);
-  cudaError_t e;
-  if (!p->hs[0]) {
-    // chunk: about 1/8 of the batch, at least 32 MiB when the batch allows
-    int64_t per = p->n * (int64_t)eb;
-    int64_t chunk = std::max<int64_t>(1, p->batch / 8);
-    chunk = std::max<int64_t>(chunk, std::min<int64_t>(p->batch, ((int64_t)32 << 20) / per));
-    p->chunk = chunk;
-    for (int i = 0; i < 2; ++i) {
-      if (!dev_alloc(p, &p->h_stage_in[i], (size_t)(chunk * p->n) * eb) ||
-          !dev_alloc(p, &p->h_stage_out[i], (size_t)(chunk * p->n) * eb))
-        return TURBOFFT_ALLOC_FAILED;
-    }
-    if (p->num_passes == 2 && !dev_alloc(p, &p->h_scratch, (size_t)(chunk * p->n) * eb)) return TURBOFFT_ALLOC_FAILED;
-    for (int i = 0; i < 3; ++i)
-      if ((e = cudaStreamCreateWithFlags(&p->hs[i], cudaStreamNonBlocking)) != cudaSuccess)
-        return cuda_fail(p, e, "stream create");
-    for (int i = 0; i < 8; ++i)
-      if ((e = cudaEventCreateWithFlags(&p->hev[i], cudaEventDisableTiming)) != cudaSuccess)
-        return cuda_fail(p, e, "event create");
+  const size_t per = (size_t)p->n * eb;
+  // chunk: whole transforms, about 64 MiB (at least one transform)
+  const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(p->batch, (int64_t)(kStageChunkBytes / per)));
+  HostStage& hs = g_stage[p->device];
+  std::lock_guard<std::mutex> lock(hs.mu);
+  cudaError_t e = stage_reserve(hs, (size_t)chunk * per);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(p, e, "exec_host staging");
   }
   cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
-  cudaStream_t sh = p->hs[0], sc = p->hs[1], sd = p->hs[2];
-  // hev[0..1] h2d done, hev[2..3] compute done, hev[4..5] d2h done, hev[6] start
-  if ((e = cudaEventRecord(p->hev[6], user)) != cudaSuccess) return cuda_fail(p, e, "event record");
-  cudaStreamWaitEvent(sh, p->hev[6], 0);
-  cudaStreamWaitEvent(sc, p->hev[6], 0);
-  cudaStreamWaitEvent(sd, p->hev[6], 0);
+  cudaStream_t sh = hs.st[0], sc = hs.st[1], sd = hs.st[2];
+  cudaEvent_t* ev = hs.ev;  // 0..1 h2d done, 2..3 transform done, 4..5 d2h done, 6 start, 7 report
+  if ((e = cudaEventRecord(ev[6], user)) != cudaSuccess) return cuda_fail(p, e, "event record");
+  cudaStreamWaitEvent(sh, ev[6], 0);
+  cudaStreamWaitEvent(sc, ev[6], 0);
+  cudaStreamWaitEvent(sd, ev[6], 0);
   const bool ft = p->ft_mode != TURBOFFT_FT_OFF;
   if (ft && (e = cudaMemsetAsync(p->d_fts, 0, tf::FT_HEADER_BYTES, sc)) != cudaSuccess)
     return cuda_fail(p, e, "report reset");
   tf::InjectSite inj = p->armed;
   p->armed.active = 0;
+  p->nprof = 0;
   const char* hin = static_cast<const char*>(host_in);
   char* hout = static_cast<char*>(host_out);
   int ci = 0;
-  for (int64_t b0 = 0; b0 < p->batch; b0 += p->chunk, ++ci) {
+  for (int64_t b0 = 0; b0 < p->batch; b0 += chunk, ++ci) {
     const int sl = ci & 1;
-    const int64_t nb = std::min<int64_t>(p->chunk, p->batch - b0);
-    const size_t off = (size_t)(b0 * p->n) * eb, bytes = (size_t)(nb * p->n) * eb;
-    if (ci >= 2) cudaStreamWaitEvent(sh, p->hev[2 + sl], 0);  // stage-in slot consumed
-    if ((e = cudaMemcpyAsync(p->h_stage_in[sl], hin + off, bytes, cudaMemcpyHostToDevice, sh)) != cudaSuccess)
+    const int64_t nb = std::min<int64_t>(chunk, p->batch - b0);
+    const size_t off = (size_t)b0 * per, bytes = (size_t)nb * per;
+    if (ci >= 2) cudaStreamWaitEvent(sh, ev[2 + sl], 0);  // stage-in slot consumed
+    if ((e = cudaMemcpyAsync(hs.in[sl], hin + off, bytes, cudaMemcpyHostToDevice, sh)) != cudaSuccess)
       return cuda_fail(p, e, "h2d");
-    cudaEventRecord(p->hev[sl], sh);
-    cudaStreamWaitEvent(sc, p->hev[sl], 0);
-    if (ci >= 2) cudaStreamWaitEvent(sc, p->hev[4 + sl], 0);  // stage-out slot drained
+    cudaEventRecord(ev[sl], sh);
+    cudaStreamWaitEvent(sc, ev[sl], 0);
+    if (ci >= 2) cudaStreamWaitEvent(sc, ev[4 + sl], 0);  // stage-out slot drained
     tf::InjectSite cinj = inj;
     if (inj.active) {
       // the armed transform belongs to exactly one chunk
-      int64_t tr = -1;
       const int kind = p->pass[inj.pass].kind;
-      if (kind == tf::KIND_SP) tr = inj.signal;
-      else if (kind == tf::KIND_COL) tr = inj.signal / p->n2;
-      else tr = inj.signal / p->n1;
-      if (tr >= b0 && tr < b0 + nb) {
-        int64_t per = (kind == tf::KIND_SP) ? 1 : (kind == tf::KIND_COL ? p->n2 : p->n1);
-        cinj.signal = inj.signal - b0 * per;
-      } else {
-        cinj.active = 0;
-      }
+      const int64_t per_tr = (kind == tf::KIND_SP) ? 1 : (kind == tf::KIND_COL ? p->n2 : p->n1);
+      const int64_t tr = inj.signal / per_tr;
+      if (tr >= b0 && tr < b0 + nb) cinj.signal = inj.signal - b0 * per_tr;
+      else cinj.active = 0;
     }
-    turbofft_status st = run(p, p->h_stage_in[sl], p->h_stage_out[sl], p->h_scratch, nb, b0, sc, cinj);
+    turbofft_status st = run(p, hs.in[sl], hs.out[sl], hs.scratch, nb, b0, sc, cinj);
     if (st != TURBOFFT_SUCCESS) return st;
-    cudaEventRecord(p->hev[2 + sl], sc);
-    cudaStreamWaitEvent(sd, p->hev[2 + sl], 0);
-    if ((e = cudaMemcpyAsync(hout + off, p->h_stage_out[sl], bytes, cudaMemcpyDeviceToHost, sd)) != cudaSuccess)
+    cudaEventRecord(ev[2 + sl], sc);
+    cudaStreamWaitEvent(sd, ev[2 + sl], 0);
+    if ((e = cudaMemcpyAsync(hout + off, hs.out[sl], bytes, cudaMemcpyDeviceToHost, sd)) != cudaSuccess)
       return cuda_fail(p, e, "d2h");
-    cudaEventRecord(p->hev[4 + sl], sd);
+    cudaEventRecord(ev[4 + sl], sd);
   }
   if (ft) {
-    cudaStreamWaitEvent(sc, p->hev[4 + ((ci - 1) & 1)], 0);
+    cudaStreamWaitEvent(sc, ev[4 + ((ci - 1) & 1)], 0);
     if ((e = cudaMemcpyAsync(p->h_fts, p->d_fts, sizeof(FtState), cudaMemcpyDeviceToHost, sc)) != cudaSuccess)
       return cuda_fail(p, e, "report copy");
-    cudaEventRecord(p->hev[7], sc);
-    cudaStreamWaitEvent(sd, p->hev[7], 0);
+    cudaEventRecord(ev[7], sc);
+    cudaStreamWaitEvent(sd, ev[7], 0);
   }
   cudaEventRecord(p->done, sd);
   cudaStreamWaitEvent(user, p->done, 0);
   p->have_exec = true;
   if ((e = cudaEventSynchronize(p->done)) != cudaSuccess) return cuda_fail(p, e, "exec_host");
+  return TURBOFFT_SUCCESS;
+}
+
+turbofft_status turbofft_set_workspace(turbofft_plan* p, void* workspace, size_t bytes) {
+  if (!p) return TURBOFFT_INVALID_VALUE;
+  if (p->num_passes == 1) return TURBOFFT_SUCCESS;  // nothing to place
+  if (!workspace || bytes < p->scratch_bytes || !aligned16(workspace)) return TURBOFFT_INVALID_VALUE;
+  if (p->scratch_owned) {
+    cudaStreamSynchronize(nullptr);
+    cudaDeviceSynchronize();
+    for (auto it = p->allocs.begin(); it != p->allocs.end(); ++it)
+      if (*it == p->d_scratch) {
+        cudaFree(*it);
+        p->allocs.erase(it);
+        p->workspace_bytes -= (int64_t)p->scratch_bytes;
+        break;
+      }
+    p->scratch_owned = false;
+  }
+  p->d_scratch = workspace;
+  return TURBOFFT_SUCCESS;
+}
+
+turbofft_status turbofft_set_profiling(turbofft_plan* p, int enable) {
+  if (!p) return TURBOFFT_INVALID_VALUE;
+  if (enable && !p->prof_ev[0][0]) {
+    for (auto& pr : p->prof_ev)
+      for (auto& e : pr) {
+        cudaError_t ce = cudaEventCreate(&e);
+        if (ce != cudaSuccess) return cuda_fail(p, ce, "event create");
+      }
+  }
+  p->profiling = enable != 0;
+  return TURBOFFT_SUCCESS;
+}
+
+turbofft_status turbofft_get_kernel_times(turbofft_plan* p, turbofft_kernel_time* out, int capacity, int* count) {
+  if (!p || !count || (capacity > 0 && !out)) return TURBOFFT_INVALID_VALUE;
+  *count = 0;
+  if (!p->profiling) return TURBOFFT_SUCCESS;
+  for (int i = 0; i < p->nprof && i < capacity; ++i) {
+    cudaError_t ce = cudaEventSynchronize(p->prof_ev[i][1]);
+    if (ce != cudaSuccess) return cuda_fail(p, ce, "profiling wait");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p->prof_ev[i][0], p->prof_ev[i][1]);
+    out[i].pass = p->prof_kind[i] / 2;
+    out[i].is_correction = p->prof_kind[i] % 2;
+    out[i].ms = ms;
+    ++*count;
+  }
   return TURBOFFT_SUCCESS;
 }
 

@@ -153,6 +153,8 @@ struct Cfg {
   static constexpr int LOG_RL = LOG_NS - (NP - 1) * LOG_E;  // log radix of the last pass
   static constexpr int B = (sizeof(c) == 8) ? 4 : 3;         // 128-byte bank row, in elements
   static constexpr int SMEM_BYTES = S * NS * (int)sizeof(c);
+  // resident blocks per SM the register allocation must allow (about 24 warps)
+  static constexpr int MINB = (768 / NT < 1) ? 1 : ((768 / NT > 8) ? 8 : 768 / NT);
   static_assert(E <= NS && NS % E == 0, "E must divide NS");
   static_assert(NT >= 32 && NT <= 1024 && NT % 32 == 0, "block size");
   static_assert(!SLOT_FAST || (32 % S == 0), "slot-fast mapping needs S | 32");
@@ -426,8 +428,68 @@ template <class K, class F> __device__ __forceinline__ void for_slot_segments(in
 
 // dynamic shared memory of the transform kernel: the exchange buffer, which
 // the checksum-group reduction reuses
-template <class K> constexpr int pass_smem_bytes() {
-  return (K::SMEM_BYTES > Seg<K>::COUNT * 64 + K::S * 4) ? K::SMEM_BYTES : (Seg<K>::COUNT * 64 + K::S * 4);
+// One stage of the shared-memory ring holds a transaction's input tile
+// (S x NS values), copied asynchronously one transaction ahead; the stage of
+// the current transaction then serves as its exchange buffer and as the
+// scratch of the checksum-group reduction.
+constexpr int NSTAGE = 2;
+template <class K> constexpr int stage_bytes() {
+  constexpr int red = Seg<K>::COUNT * 64 + K::S * 4;
+  constexpr int b = (K::SMEM_BYTES > red) ? K::SMEM_BYTES : red;
+  return (b + 127) / 128 * 128;
+}
+template <class K> constexpr int pass_smem_bytes() { return NSTAGE * stage_bytes<K>(); }
+
+// ---------------------------------------------------------------------------
+// asynchronous global -> shared copies (cp.async, 16 bytes, L2 only)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Issue the copies of work unit `unit`'s input tile into `stage`.  Layout in
+// shared memory: slot-major [slot][pos] for SP/ROW (contiguous in global
+// memory), position-major [pos][slot] for COL (S adjacent columns of each
+// row are contiguous).  Units past the end issue nothing; a ragged last SP
+// unit copies only its valid transforms.
+template <class K>
+__device__ __forceinline__ void issue_unit(const PassArgs<typename K::real>& A, long long unit, char* stage,
+                                           int tid) {
+  using c = typename K::c;
+  const Geo& g = A.geo;
+  if constexpr (K::KIND == KIND_SP) {
+    const long long first = unit * K::S;
+    long long nv = g.batch - first;
+    if (nv > K::S) nv = K::S;
+    const char* src = reinterpret_cast<const char*>(A.in + first * K::NS);
+    const int chunks = (int)(nv * K::NS * (long long)sizeof(c) / 16);
+    for (int q = tid; q < chunks; q += K::NT) cp_async16(stage + 16 * q, src + 16 * (size_t)q);
+  } else if constexpr (K::KIND == KIND_ROW) {
+    const int blocks = g.n1 / K::S;
+    const long long b = unit / blocks;
+    const int r0 = (int)(unit - b * blocks) * K::S;
+    const char* src = reinterpret_cast<const char*>(A.in + b * g.n + (long long)r0 * g.n2);
+    constexpr int chunks = K::S * K::NS * (int)sizeof(c) / 16;
+    for (int q = tid; q < chunks; q += K::NT) cp_async16(stage + 16 * q, src + 16 * (size_t)q);
+  } else {
+    const int blocks = g.n2 / K::S;
+    const long long b = unit / blocks;
+    const int c0 = (int)(unit - b * blocks) * K::S;
+    constexpr int cpr = K::S * (int)sizeof(c) / 16;  // 16-byte chunks per row of the tile
+    static_assert(cpr >= 1, "a column tile row must span 16 bytes");
+    const c* base = A.in + b * g.n + c0;
+    constexpr int chunks = K::NS * cpr;
+    for (int q = tid; q < chunks; q += K::NT) {
+      const int p = q / cpr, j = q - p * cpr;
+      cp_async16(stage + (size_t)p * K::S * sizeof(c) + 16 * j,
+                 reinterpret_cast<const char*>(base + (long long)p * g.n2) + 16 * j);
+    }
+  }
 }
 
 __device__ __forceinline__ void atomic_max_nonneg(float* addr, float v) {
@@ -437,13 +499,18 @@ __device__ __forceinline__ void atomic_max_nonneg(float* addr, float v) {
 // ---------------------------------------------------------------------------
 // the transform kernel (one pass)
 // ---------------------------------------------------------------------------
-template <class K, bool FT>
-__global__ void __launch_bounds__(K::NT) tf_pass_kernel(const PassArgs<typename K::real> A) {
+// FTM: 0 = no checksums; 1 = checksums, right-side sums formed on the rare
+// path from HBM; 2 = checksums, right-side sums kept in registers during the
+// pass (the thread-level accumulation of Sec. 4.3)
+template <class K, int FTM>
+__global__ void __launch_bounds__(K::NT, K::MINB) tf_pass_kernel(const PassArgs<typename K::real> A) {
   using R = typename K::real;
   using c = typename K::c;
   constexpr int E = K::E, P = K::P, S = K::S;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  c* sm = reinterpret_cast<c*>(smem_raw);
+  constexpr bool FT = FTM != 0;
+  constexpr bool EAGER = FTM == 2;
+  extern __shared__ __align__(128) unsigned char smem_raw_[];
+  char* smem_raw = reinterpret_cast<char*>(smem_raw_);
 
   const int tid = threadIdx.x;
   const int slot = K::SLOT_FAST ? (tid % S) : (tid / P);
@@ -452,35 +519,55 @@ __global__ void __launch_bounds__(K::NT) tf_pass_kernel(const PassArgs<typename 
   const long long stride = gridDim.x;
 
   // checksum-group state (per thread)
-  c xs[FT ? E : 1], ys[FT ? E : 1];
+  c xs[EAGER ? E : 1], ys[EAGER ? E : 1];
   R s1r = 0, s1i = 0, s2r = 0, s2i = 0, en = 0;
   int bad_lo = 0x7fffffff, bad_hi = -1;
   int gi = 0;                     // transaction index inside the group
   long long g_unit0 = blockIdx.x;
   long long groups = 0;
   float max_ratio = 0.f;
-  if constexpr (FT) {
+  if constexpr (EAGER) {
 #pragma unroll
     for (int i = 0; i < E; ++i) { xs[i] = mk<c>(0, 0); ys[i] = mk<c>(0, 0); }
   }
 
-  for (long long unit = blockIdx.x; unit < A.num_units; unit += stride) {
+  // prologue: the first NSTAGE-1 transactions' tiles in flight
+#pragma unroll
+  for (int k = 0; k < NSTAGE - 1; ++k) {
+    const long long u = blockIdx.x + k * stride;
+    if (u < A.num_units) issue_unit<K>(A, u, smem_raw + k * stage_bytes<K>(), tid);
+    cp_async_commit();
+  }
+  int it = 0;
+  for (long long unit = blockIdx.x; unit < A.num_units; unit += stride, ++it) {
+    // prefetch NSTAGE-1 transactions ahead into the stage freed by the
+    // previous transaction, then wait for this transaction's tile
+    {
+      const long long un = unit + (NSTAGE - 1) * stride;
+      if (un < A.num_units) issue_unit<K>(A, un, smem_raw + ((it + NSTAGE - 1) % NSTAGE) * stage_bytes<K>(), tid);
+      cp_async_commit();
+      cp_async_wait<NSTAGE - 1>();
+      __syncthreads();
+    }
+    c* sm = reinterpret_cast<c*>(smem_raw + (it % NSTAGE) * stage_bytes<K>());
     const long long sig = signal_of<K>(g, unit, slot);
     const bool valid = sig >= 0;
     c a[E];
-    // ---- load (coalesced across the threads of a slot, or across slots)
+    // ---- home positions from the staged tile
 #pragma unroll
     for (int i = 0; i < E; ++i) {
       c v = mk<c>(0, 0);
-      if (valid) v = A.in[in_off<K>(g, sig, t + i * P)];
+      const int pos = t + i * P;
+      if (valid) v = K::SLOT_FAST ? sm[pos * S + slot] : sm[slot * K::NS + pos];
       a[i] = A.conj_in ? cconj(v) : v;
     }
+    __syncthreads();  // the tile is consumed; the stage becomes the exchange buffer
     // ---- input side of the checksums
     c pin = mk<c>(0, 0);
     if constexpr (FT) {
 #pragma unroll
       for (int i = 0; i < E; ++i) {
-        xs[i] = cadd(xs[i], a[i]);
+        if constexpr (EAGER) xs[i] = cadd(xs[i], a[i]);
         cmac(pin, ldg(A.vv + t + i * P), a[i]);
         en += a[i].x * a[i].x + a[i].y * a[i].y;
       }
@@ -503,14 +590,12 @@ __global__ void __launch_bounds__(K::NT) tf_pass_kernel(const PassArgs<typename 
       const int pos = t + i * P;
       if constexpr (K::KIND == KIND_COL) {
         const c w = colTwiddle<K>(g, A.tlo, A.thi, valid ? sig : 0, pos);
-        if constexpr (FT) ys[i] = cadd(ys[i], a[i]);
+        if constexpr (EAGER) ys[i] = cadd(ys[i], a[i]);
         a[i] = cmul(a[i], w);
         if constexpr (FT) cmac(pout, cmul(ldg(A.ev + pos), cconj(w)), a[i]);
       } else {
-        if constexpr (FT) {
-          ys[i] = cadd(ys[i], a[i]);
-          cmac(pout, ldg(A.ev + pos), a[i]);
-        }
+        if constexpr (EAGER) ys[i] = cadd(ys[i], a[i]);
+        if constexpr (FT) cmac(pout, ldg(A.ev + pos), a[i]);
       }
     }
     // ---- store
@@ -528,7 +613,7 @@ __global__ void __launch_bounds__(K::NT) tf_pass_kernel(const PassArgs<typename 
         c v = sm[s2 * K::NS + (pos ^ (s2 & ((1 << K::B) - 1)))];
         if (A.conj_out) v = cconj(v);
         v = cscale(v, A.out_scale);
-        A.out[out_off<K>(g, sig2, pos)] = v;
+        __stcs(A.out + out_off<K>(g, sig2, pos), v);  // streaming: keep L1 for the tables
       }
       __syncthreads();
     } else {
@@ -538,7 +623,7 @@ __global__ void __launch_bounds__(K::NT) tf_pass_kernel(const PassArgs<typename 
           c v = a[i];
           if (A.conj_out) v = cconj(v);
           v = cscale(v, A.out_scale);
-          A.out[out_off<K>(g, sig, t + i * P)] = v;
+          __stcs(A.out + out_off<K>(g, sig, t + i * P), v);
         }
       }
     }
@@ -560,8 +645,8 @@ __global__ void __launch_bounds__(K::NT) tf_pass_kernel(const PassArgs<typename 
       if (group_end) {
         // ---- reduce the group over the threads of each slot
         __syncthreads();  // the exchange buffer is free now
-        double* red = reinterpret_cast<double*>(smem_raw);
-        int* flag = reinterpret_cast<int*>(smem_raw + (size_t)Seg<K>::COUNT * 8 * sizeof(double));
+        double* red = reinterpret_cast<double*>(sm);
+        int* flag = reinterpret_cast<int*>(reinterpret_cast<char*>(sm) + (size_t)Seg<K>::COUNT * 8 * sizeof(double));
         R v0 = seg_reduce_sum<K>(s1r), v1 = seg_reduce_sum<K>(s1i);
         R v2 = seg_reduce_sum<K>(s2r), v3 = seg_reduce_sum<K>(s2i);
         R v4 = seg_reduce_sum<K>(en);
@@ -615,6 +700,7 @@ __global__ void __launch_bounds__(K::NT) tf_pass_kernel(const PassArgs<typename 
               R0.tau = tau;
               R0.energy = EN;
               R0.result = FT_RES_PENDING;
+              R0.has_sums = EAGER ? 1 : 0;
               R0.signal = -1;
               rec = (int)r;
             } else {
@@ -624,18 +710,20 @@ __global__ void __launch_bounds__(K::NT) tf_pass_kernel(const PassArgs<typename 
           flag[tid] = rec;
         }
         __syncthreads();
-        const int myrec = flag[slot];
-        if (myrec >= 0) {
-          // right-side sums of this slot -> the record, for delayed correction
-          c* xr = reinterpret_cast<c*>(A.rec_sums) + (size_t)myrec * 2 * A.rec_stride;
-          c* yr = xr + A.rec_stride;
+        if constexpr (EAGER) {
+          const int myrec = flag[slot];
+          if (myrec >= 0) {
+            // right-side sums of this slot -> the record, for delayed correction
+            c* xr = reinterpret_cast<c*>(A.rec_sums) + (size_t)myrec * 2 * A.rec_stride;
+            c* yr = xr + A.rec_stride;
 #pragma unroll
-          for (int i = 0; i < E; ++i) { xr[t + i * P] = xs[i]; yr[t + i * P] = ys[i]; }
+            for (int i = 0; i < E; ++i) { xr[t + i * P] = xs[i]; yr[t + i * P] = ys[i]; }
+          }
+#pragma unroll
+          for (int i = 0; i < E; ++i) { xs[i] = mk<c>(0, 0); ys[i] = mk<c>(0, 0); }
         }
         __syncthreads();
         ++groups;
-#pragma unroll
-        for (int i = 0; i < E; ++i) { xs[i] = mk<c>(0, 0); ys[i] = mk<c>(0, 0); }
         s1r = s1i = s2r = s2i = en = 0;
         bad_lo = 0x7fffffff;
         bad_hi = -1;
@@ -804,19 +892,35 @@ __global__ void __launch_bounds__(K::NT) tf_fix_kernel(const PassArgs<typename K
 
     // (1) the paper's correction from the right-side sums:
     //     Delta = y_bar - W x_bar, y_k <- y_k - Delta
+    //     (sums kept by the transform kernel, or formed here from the
+    //     group's untouched inputs and stored outputs)
     int how = 0;
     {
-      const c* xr = reinterpret_cast<const c*>(A.rec_sums) + (size_t)r * 2 * A.rec_stride;
-      const c* yr = xr + A.rec_stride;
-      c a[E];
+      c a[E], yb[E];
+      if (rec.has_sums) {
+        const c* xr = reinterpret_cast<const c*>(A.rec_sums) + (size_t)r * 2 * A.rec_stride;
+        const c* yr = xr + A.rec_stride;
 #pragma unroll
-      for (int i = 0; i < E; ++i) a[i] = xr[t + i * P];
+        for (int i = 0; i < E; ++i) { a[i] = xr[t + i * P]; yb[i] = yr[t + i * P]; }
+      } else {
+#pragma unroll
+        for (int i = 0; i < E; ++i) { a[i] = mk<c>(0, 0); yb[i] = mk<c>(0, 0); }
+        for (int kk = 0; kk < rec.count; ++kk) {
+          const long long s = sig_of(kk);
+          if (s < 0) continue;
+          c xv[E], yv[E];
+          load_input<K>(A, s, t, xv);
+          load_output_internal<K>(A, s, t, yv);
+#pragma unroll
+          for (int i = 0; i < E; ++i) { a[i] = cadd(a[i], xv[i]); yb[i] = cadd(yb[i], yv[i]); }
+        }
+      }
       fft_block<K>(a, sm, A.tw, slot, t);
       c cand[E];
       bool fin = true;
 #pragma unroll
       for (int i = 0; i < E; ++i) {
-        const c d = csub(yr[t + i * P], a[i]);
+        const c d = csub(yb[i], a[i]);
         cand[i] = csub(y_old[i], d);
         fin = fin && isfinite(cand[i].x) && isfinite(cand[i].y);
       }

@@ -6,12 +6,8 @@
 
 namespace tf {
 
-template <class K> void launch_plain(const void* a, int grid, cudaStream_t s) {
-  tf_pass_kernel<K, false><<<grid, K::NT, pass_smem_bytes<K>(), s>>>(
-      *static_cast<const PassArgs<typename K::real>*>(a));
-}
-template <class K> void launch_ft(const void* a, int grid, cudaStream_t s) {
-  tf_pass_kernel<K, true><<<grid, K::NT, pass_smem_bytes<K>(), s>>>(
+template <class K, int FTM> void launch_main(const void* a, int grid, cudaStream_t s) {
+  tf_pass_kernel<K, FTM><<<grid, K::NT, pass_smem_bytes<K>(), s>>>(
       *static_cast<const PassArgs<typename K::real>*>(a));
 }
 template <class K> void launch_fix(const void* a, int grid, cudaStream_t s) {
@@ -29,11 +25,13 @@ template <class K> KernelEntry make_entry() {
   e.stages = K::NP;
   e.smem_main = pass_smem_bytes<K>();
   e.smem_fix = K::SMEM_BYTES;
-  e.main_plain = &launch_plain<K>;
-  e.main_ft = &launch_ft<K>;
+  e.main[0] = &launch_main<K, 0>;
+  e.main[1] = &launch_main<K, 1>;
+  e.main[2] = &launch_main<K, 2>;
   e.fix = &launch_fix<K>;
-  e.fn_plain = reinterpret_cast<const void*>(&tf_pass_kernel<K, false>);
-  e.fn_ft = reinterpret_cast<const void*>(&tf_pass_kernel<K, true>);
+  e.fn_main[0] = reinterpret_cast<const void*>(&tf_pass_kernel<K, 0>);
+  e.fn_main[1] = reinterpret_cast<const void*>(&tf_pass_kernel<K, 1>);
+  e.fn_main[2] = reinterpret_cast<const void*>(&tf_pass_kernel<K, 2>);
   e.fn_fix = reinterpret_cast<const void*>(&tf_fix_kernel<K>);
   return e;
 }

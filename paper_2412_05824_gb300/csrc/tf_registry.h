@@ -17,9 +17,9 @@ struct KernelEntry {
   int stages;       // radix passes
   int smem_main;    // dynamic shared memory of the transform kernel
   int smem_fix;     // dynamic shared memory of the correction kernel
-  LaunchFn main_plain, main_ft, fix;
-  const void* fn_plain;
-  const void* fn_ft;
+  LaunchFn main[3];   // transform kernel: no checksums / checksums / checksums + register sums
+  LaunchFn fix;       // correction kernel
+  const void* fn_main[3];
   const void* fn_fix;
 };
 

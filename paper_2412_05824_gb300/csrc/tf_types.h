@@ -41,7 +41,7 @@ struct FtRecord {
   long long transform_base;  // offset of the launch's first transform in the caller's batch
   double s1r, s1i, s2r, s2i, tau, energy;
   int result;         // FtResult
-  int pad;
+  int has_sums;       // right-side sums stored with the record (register mode)
   long long signal;   // sub-transform id of the located signal (-1 if none)
 };
 

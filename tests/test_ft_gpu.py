@@ -35,7 +35,7 @@ class Runner:
             self.ref = oracle.fft(self.x, inverse=True, scaled=direction == "inverse")
         self.tol = oracle.tolerance(DT[dt], n)
         self.plans = {m: tfl.Plan(n, batch, "complex64" if dt == "c64" else "complex128", direction, m)
-                      for m in ("off", "detect", "correct")}
+                      for m in ("off", "detect", "correct", "correct_registers")}
 
     def run(self, mode, site=None, bit=None):
         p = self.plans[mode]
@@ -119,6 +119,27 @@ def test_mantissa_flips(dt, n, batch):
         else:
             assert float(np.max(err)) <= r.tol
     assert escapes <= 1
+
+
+@pytest.mark.parametrize("dt,n,batch", [("c64", 512, 50), ("c64", 1 << 15, 5), ("c128", 1024, 11)])
+def test_register_sums_mode_matches(dt, n, batch):
+    """Right-side sums kept in registers (the paper's thread-level
+    accumulation): the same detections and corrections."""
+    r = Runner(n, batch, dt)
+    rng = np.random.default_rng(7 * n)
+    bit = 30 if dt == "c64" else 62
+    for (tr, p, st, el, comp, b) in _sites(r, rng, 8, [bit] + list(range(16, 21))):
+        _, err_off, _ = r.run("off", (tr, p, st, el, comp), b)
+        y1, err1, rep1 = r.run("correct", (tr, p, st, el, comp), b)
+        y2, err2, rep2 = r.run("correct_registers", (tr, p, st, el, comp), b)
+        assert rep1["detected"] == rep2["detected"]
+        assert rep1["corrected"] == rep2["corrected"] and rep1["uncorrectable"] == rep2["uncorrectable"] == 0
+        if rep1["detected"]:
+            assert rep1["first_transform"] == rep2["first_transform"] == tr
+        assert float(np.max(err1)) <= r.tol and float(np.max(err2)) <= r.tol
+    for _ in range(5):
+        _, err, rep = r.run("correct_registers")
+        assert rep["detected"] == 0 and float(np.max(err)) <= r.tol
 
 
 @pytest.mark.parametrize("dt,n,batch", [("c64", 1024, 40), ("c64", 1 << 18, 2), ("c128", 2048, 9)])
