@@ -234,6 +234,32 @@ turbofft_status turbofft_set_profiling(turbofft_plan *plan, int enable);
 turbofft_status turbofft_get_kernel_times(turbofft_plan *plan, turbofft_kernel_time *out,
                                           int capacity, int *count);
 
+/*
+ * No counterpart in the paper: a library facility, not part of the method.
+ *
+ * turbofft_exec without any device allocation, for callers that create
+ * their plans ahead of time but cannot call cudaMalloc (or any allocating
+ * routine) when they transform -- e.g. a program whose device memory belongs
+ * to another allocator that hands out no raw buffers, or one running under a
+ * device-memory budget fixed at start-up.  A two-pass plan's intermediate
+ * (info.scratch_bytes) is placed in a file-scope device array of
+ * TURBOFFT_STATIC_SCRATCH_BYTES that the library keeps on every GPU where
+ * this part of it is loaded, until the process exits; one-pass plans need
+ * no intermediate.  Same results as turbofft_exec.
+ *   - Plans needing more than TURBOFFT_STATIC_SCRATCH_BYTES are rejected with
+ *     TURBOFFT_INVALID_VALUE (message in turbofft_last_error); nothing runs.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - All calls on a device share the array: calls whose kernels may overlap
+ *     on the GPU (e.g. on unordered streams) race on it.  Its contents carry
+ *     over between calls and need no clearing: every element is written
+ *     before it is read within one call.
+ *   - in, out, stream: as turbofft_exec.
+ */
+#define TURBOFFT_STATIC_SCRATCH_BYTES (32u << 20)
+turbofft_status turbofft_exec_static_scratch(turbofft_plan *plan, const void *in, void *out,
+                                             turbofft_stream stream);
+
 /* Free everything the plan owns.  NULL is a no-op.  Waits for the plan's
  * outstanding work first. */
 turbofft_status turbofft_destroy(turbofft_plan *plan);

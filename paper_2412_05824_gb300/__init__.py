@@ -77,7 +77,10 @@ EXPORTS = [
     "turbofft_get_report", "turbofft_plan_get_info", "turbofft_set_threshold_scale",
     "turbofft_destroy", "turbofft_status_string", "turbofft_last_error",
     "turbofft_set_workspace", "turbofft_set_profiling", "turbofft_get_kernel_times",
+    "turbofft_exec_static_scratch",
 ]
+
+STATIC_SCRATCH_BYTES = 32 << 20
 
 _lib = None
 
@@ -94,6 +97,7 @@ def lib() -> ctypes.CDLL:
     L.turbofft_plan_create.argtypes = [i64, i64, i32, i32, i32, ctypes.POINTER(vp)]
     L.turbofft_exec.argtypes = [vp, vp, vp, vp]
     L.turbofft_exec_host.argtypes = [vp, vp, vp, vp]
+    L.turbofft_exec_static_scratch.argtypes = [vp, vp, vp, vp]
     L.turbofft_inject.argtypes = [vp, Site, i32]
     L.turbofft_get_report.argtypes = [vp, ctypes.POINTER(Report)]
     L.turbofft_plan_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]

@@ -18,6 +18,7 @@ LIB = os.path.join(HERE, "libturbofft.so")
 
 SOURCES = [
     "tf_capi.cu",
+    "tf_noalloc.cu",
     "tf_k_f32_sp.cu",
     "tf_k_f32_col.cu",
     "tf_k_f32_row.cu",

@@ -20,6 +20,7 @@
 
 #include "../../include/turbofft.h"
 #include "tf_device.cuh"
+#include "tf_internal.h"
 #include "tf_registry.h"
 
 using tf::FtRecord;
@@ -771,3 +772,44 @@ turbofft_status turbofft_get_report(turbofft_plan* p, turbofft_report* r) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// library-internal helpers (tf_internal.h)
+// ---------------------------------------------------------------------------
+namespace tf {
+
+size_t plan_scratch_bytes(const turbofft_plan* p) { return p->num_passes == 2 ? p->scratch_bytes : 0; }
+
+int plan_device(const turbofft_plan* p) { return p->device; }
+
+void plan_set_error(turbofft_plan* p, const char* msg) { p->last_error = msg; }
+
+turbofft_status exec_given_scratch(turbofft_plan* p, const void* in, void* out, void* scratch, cudaStream_t s) {
+  if (!p || !in || !out) return TURBOFFT_INVALID_VALUE;
+  if (!aligned16(in) || !aligned16(out)) return TURBOFFT_INVALID_VALUE;
+  if (p->num_passes == 2 && (!scratch || !aligned16(scratch))) return TURBOFFT_INVALID_VALUE;
+  const size_t bytes = (size_t)(p->batch * p->n) * elem_bytes(p->dtype);
+  const char* a = static_cast<const char*>(in);
+  const char* b = static_cast<const char*>(out);
+  if (a < b + bytes && b < a + bytes) return TURBOFFT_UNSUPPORTED;
+  const bool ft = p->ft_mode != TURBOFFT_FT_OFF;
+  if (ft) {
+    cudaError_t e = cudaMemsetAsync(p->d_fts, 0, tf::FT_HEADER_BYTES, s);
+    if (e != cudaSuccess) return cuda_fail(p, e, "report reset");
+  }
+  tf::InjectSite inj = p->armed;
+  p->armed.active = 0;
+  p->nprof = 0;
+  turbofft_status st = run(p, in, out, scratch, p->batch, 0, s, inj);
+  if (st != TURBOFFT_SUCCESS) return st;
+  if (ft) {
+    cudaError_t e = cudaMemcpyAsync(p->h_fts, p->d_fts, sizeof(FtState), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(p, e, "report copy");
+  }
+  cudaError_t e = cudaEventRecord(p->done, s);
+  if (e != cudaSuccess) return cuda_fail(p, e, "event record");
+  p->have_exec = true;
+  return TURBOFFT_SUCCESS;
+}
+
+}  // namespace tf
