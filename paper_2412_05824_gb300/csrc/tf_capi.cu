@@ -151,6 +151,8 @@ struct PassPlan {
   void* d_tw = nullptr;
   void* d_ev = nullptr;
   void* d_vv = nullptr;
+  void* d_ev4 = nullptr;  // float32: (re, re, im, im) arrangement for paired FMAs
+  void* d_vv4 = nullptr;
   double tau_coef = 0;
 };
 
@@ -222,8 +224,19 @@ bool upload_tables(turbofft_plan* p, PassPlan& pp) {
   std::vector<cld> e = encoding_vector(ns);
   std::vector<cld> v = e;
   host_fft(v);  // v = W e = (e^T W)^T, W symmetric (Eq. 1)
-  if (p->dtype == TURBOFFT_C2C_F32)
-    return upload<float>(p, &pp.d_tw, tw) && upload<float>(p, &pp.d_ev, e) && upload<float>(p, &pp.d_vv, v);
+  if (p->dtype == TURBOFFT_C2C_F32) {
+    auto arranged = [&](void** dst, const std::vector<cld>& src) {
+      std::vector<float4> t4(src.size());
+      for (size_t i = 0; i < src.size(); ++i) {
+        const float re = (float)src[i].real(), im = (float)src[i].imag();
+        t4[i] = make_float4(re, re, im, im);
+      }
+      const size_t bytes = t4.size() * sizeof(float4);
+      return dev_alloc(p, dst, bytes) && cudaMemcpy(*dst, t4.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    return upload<float>(p, &pp.d_tw, tw) && upload<float>(p, &pp.d_ev, e) && upload<float>(p, &pp.d_vv, v) &&
+           arranged(&pp.d_ev4, e) && arranged(&pp.d_vv4, v);
+  }
   return upload<double>(p, &pp.d_tw, tw) && upload<double>(p, &pp.d_ev, e) && upload<double>(p, &pp.d_vv, v);
 }
 
@@ -233,7 +246,7 @@ int ft_variant(int ft_mode) { return ft_mode == TURBOFFT_FT_OFF ? 0 : (ft_mode =
 int occupancy_blocks(const KernelEntry* ke, int variant) {
   int nb = 0;
   const void* fn = ke->fn_main[variant];
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, ke->nt, ke->smem_main) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, ke->nt, ke->smem_main[variant]) != cudaSuccess) {
     cudaGetLastError();
     nb = 1;
   }
@@ -243,7 +256,7 @@ int occupancy_blocks(const KernelEntry* ke, int variant) {
 bool set_smem_attrs(const KernelEntry* ke) {
   // the attribute is per function; setting it again is harmless
   for (int v = 0; v < 3; ++v)
-    if (cudaFuncSetAttribute(ke->fn_main[v], cudaFuncAttributeMaxDynamicSharedMemorySize, ke->smem_main) !=
+    if (cudaFuncSetAttribute(ke->fn_main[v], cudaFuncAttributeMaxDynamicSharedMemorySize, ke->smem_main[v]) !=
         cudaSuccess)
       return false;
   if (cudaFuncSetAttribute(ke->fn_fix, cudaFuncAttributeMaxDynamicSharedMemorySize, ke->smem_fix) != cudaSuccess)
@@ -269,6 +282,8 @@ void fill_args(const turbofft_plan* p, int pi, const void* in, void* out, int64_
   A.tw = static_cast<const c*>(pp.d_tw);
   A.ev = static_cast<const c*>(pp.d_ev);
   A.vv = static_cast<const c*>(pp.d_vv);
+  A.ev4 = static_cast<const float4*>(pp.d_ev4);
+  A.vv4 = static_cast<const float4*>(pp.d_vv4);
   A.tlo = static_cast<const c*>(p->d_tlo);
   A.thi = static_cast<const c*>(p->d_thi);
   A.geo.n = p->n;

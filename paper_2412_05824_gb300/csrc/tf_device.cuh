@@ -62,12 +62,19 @@ template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk<C>
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
   return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
+// float32 complex add / subtract as one paired FP32 instruction each
+// (sm_100+ FADD2: two independent round-to-nearest additions, the same
+// results as the scalar code)
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 template <typename C> __device__ __forceinline__ C cconj(C a) { return mk<C>(a.x, -a.y); }
 template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return mk<C>(a.x * s, a.y * s); }
-// acc += a*b
+// acc += a*b as four chained fused multiply-adds
 template <typename C> __device__ __forceinline__ void cmac(C& acc, C a, C b) {
-  acc.x += a.x * b.x - a.y * b.y;
-  acc.y += a.x * b.y + a.y * b.x;
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
 }
 
 template <typename C> __device__ __forceinline__ C ldg(const C* p) { return __ldg(p); }
@@ -153,8 +160,7 @@ struct Cfg {
   static constexpr int LOG_RL = LOG_NS - (NP - 1) * LOG_E;  // log radix of the last pass
   static constexpr int B = (sizeof(c) == 8) ? 4 : 3;         // 128-byte bank row, in elements
   static constexpr int SMEM_BYTES = S * NS * (int)sizeof(c);
-  // resident blocks per SM the register allocation must allow (about 24 warps)
-  static constexpr int MINB = (768 / NT < 1) ? 1 : ((768 / NT > 8) ? 8 : 768 / NT);
+
   static_assert(E <= NS && NS % E == 0, "E must divide NS");
   static_assert(NT >= 32 && NT <= 1024 && NT % 32 == 0, "block size");
   static_assert(!SLOT_FAST || (32 % S == 0), "slot-fast mapping needs S | 32");
@@ -210,9 +216,82 @@ template <class K> __device__ __forceinline__ void inject_stage(typename K::c (&
   }
 }
 
-template <class K, int p>
-__device__ __forceinline__ void run_pass(typename K::c (&a)[K::E], typename K::c* sm,
-                                         const typename K::c* __restrict__ tw, int slot, int t) {
+// Pass twiddles of one thread.  Thread t's butterflies j = t + u*P need
+// w_NS^{TWS*(j mod L)*m}, the same values in every transaction, so when
+// they fit in a register budget they are loaded once per block and kept in
+// registers; otherwise they are read from the table in each pass.
+template <class K, int p> struct TwCount {
+  static constexpr int v = (PassInfo<K, p>::L > 1) ? PassInfo<K, p>::NB * (PassInfo<K, p>::R - 1) : 0;
+};
+template <class K, int p> struct TwOff { static constexpr int v = TwOff<K, p - 1>::v + TwCount<K, p - 1>::v; };
+template <class K> struct TwOff<K, 0> { static constexpr int v = 0; };
+template <class K> struct TwTotal { static constexpr int v = TwOff<K, K::NP>::v; };
+#ifndef TF_FT_TW_BUDGET
+#define TF_FT_TW_BUDGET 64
+#endif
+template <class K, int BUDGET = 64> struct TwMode {
+  // passes whose twiddles fit, in order, in BUDGET 32-bit registers keep
+  // them in registers; later passes read the table
+  template <int p> static constexpr bool reg() {
+    return TwOff<K, p + 1>::v * (int)sizeof(typename K::c) / 4 <= BUDGET;
+  }
+  static constexpr int count_reg() {
+    int n = 0;
+    for (int p = 0; p < K::NP; ++p) {
+      int off = 0, cnt = 0;
+      // recompute offsets without templates
+      for (int q = 0; q <= p; ++q) {
+        const int lr = (q == K::NP - 1) ? K::LOG_RL : K::LOG_E;
+        const int L = 1 << (q * K::LOG_E), R = 1 << lr, NB = K::E / R;
+        cnt = (L > 1) ? NB * (R - 1) : 0;
+        off += cnt;
+      }
+      if (off * (int)sizeof(typename K::c) / 4 <= BUDGET) n = off;
+    }
+    return n;
+  }
+  static constexpr int N = count_reg() > 0 ? count_reg() : 1;
+  static constexpr bool ANY = count_reg() > 0;
+  // resident blocks per SM that the register allocation must allow
+  static constexpr int MINB_RAW = (ANY ? 512 : 768) / K::NT;
+  static constexpr int MINB = MINB_RAW < 1 ? 1 : (MINB_RAW > 8 ? 8 : MINB_RAW);
+#ifndef TF_FT_MINB_DELTA
+#define TF_FT_MINB_DELTA 0
+#endif
+  // checksum variants: optionally fewer resident blocks for more registers
+  static constexpr int MINB_FT = (MINB - TF_FT_MINB_DELTA) < 1 ? 1 : (MINB - TF_FT_MINB_DELTA);
+};
+
+template <class K, int BUDGET = 64> struct TwReg {
+  using c = typename K::c;
+  using M = TwMode<K, BUDGET>;
+  c v[M::N];
+  const c* __restrict__ tab;
+  __device__ __forceinline__ void load(const c* __restrict__ tw, int t) {
+    tab = tw;
+    static_for<0, K::NP>([&](auto pc) {
+      constexpr int p = decltype(pc)::value;
+      using PI = PassInfo<K, p>;
+      if constexpr (PI::L > 1 && M::template reg<p>()) {
+#pragma unroll
+        for (int u = 0; u < PI::NB; ++u) {
+          const int k = (t + u * K::P) & (PI::L - 1);
+#pragma unroll
+          for (int m = 1; m < PI::R; ++m) v[TwOff<K, p>::v + u * (PI::R - 1) + m - 1] = ldg(tw + PI::TWS * k * m);
+        }
+      }
+    });
+  }
+  template <int p> __device__ __forceinline__ c get(int u, int m, int k) const {
+    using PI = PassInfo<K, p>;
+    if constexpr (M::template reg<p>()) return v[TwOff<K, p>::v + u * (PI::R - 1) + m - 1];
+    else return ldg(tab + PI::TWS * k * m);
+  }
+};
+
+template <class K, int p, class TW>
+__device__ __forceinline__ void run_pass(typename K::c (&a)[K::E], typename K::c* sm, const TW& tw, int slot,
+                                         int t) {
   using c = typename K::c;
   using PI = PassInfo<K, p>;
   constexpr int R = PI::R, NB = PI::NB, L = PI::L;
@@ -225,7 +304,7 @@ __device__ __forceinline__ void run_pass(typename K::c (&a)[K::E], typename K::c
     for (int m = 0; m < R; ++m) b[m] = a[u + m * NB];
     if constexpr (L > 1) {
 #pragma unroll
-      for (int m = 1; m < R; ++m) b[m] = cmul(b[m], ldg(tw + PI::TWS * k * m));
+      for (int m = 1; m < R; ++m) b[m] = cmul(b[m], tw.template get<p>(u, m, k));
     }
     Dft<c, R>::run(b);
     if constexpr (PI::LAST) {
@@ -246,17 +325,17 @@ __device__ __forceinline__ void run_pass(typename K::c (&a)[K::E], typename K::c
 }
 
 template <class K, int p, bool END = (p == K::NP)> struct Passes {
-  static __device__ __forceinline__ void run(typename K::c (&a)[K::E], typename K::c* sm,
-                                             const typename K::c* __restrict__ tw, int slot, int t,
-                                             const InjCtx& ic) {
+  template <class TW>
+  static __device__ __forceinline__ void run(typename K::c (&a)[K::E], typename K::c* sm, const TW& tw, int slot,
+                                             int t, const InjCtx& ic) {
     inject_stage<K>(a, p, ic, t);
-    run_pass<K, p>(a, sm, tw, slot, t);
+    run_pass<K, p, TW>(a, sm, tw, slot, t);
     Passes<K, p + 1>::run(a, sm, tw, slot, t, ic);
   }
 };
 template <class K, int p> struct Passes<K, p, true> {
-  static __device__ __forceinline__ void run(typename K::c (&a)[K::E], typename K::c*,
-                                             const typename K::c* __restrict__, int, int t,
+  template <class TW>
+  static __device__ __forceinline__ void run(typename K::c (&a)[K::E], typename K::c*, const TW&, int, int t,
                                              const InjCtx& ic) {
     inject_stage<K>(a, p, ic, t);
   }
@@ -264,9 +343,9 @@ template <class K, int p> struct Passes<K, p, true> {
 
 // full sub-transform in registers + shared memory (all threads of the block
 // take part; no injection)
-template <class K>
-__device__ __forceinline__ void fft_block(typename K::c (&a)[K::E], typename K::c* sm,
-                                          const typename K::c* __restrict__ tw, int slot, int t) {
+template <class K, class TW>
+__device__ __forceinline__ void fft_block(typename K::c (&a)[K::E], typename K::c* sm, const TW& tw, int slot,
+                                          int t) {
   InjCtx off{false, 0, 0, 0, 0};
   Passes<K, 0>::run(a, sm, tw, slot, t, off);
 }
@@ -345,6 +424,8 @@ template <typename R> struct PassArgs {
   const c* tw;    // w_NS^q, q < NS (forward sign)
   const c* ev;    // output-side encoding vector e, NS entries
   const c* vv;    // input-side vector v = W^T e, NS entries
+  const float4* ev4;  // float32 plans: e arranged as (re, re, im, im) for paired FMAs
+  const float4* vv4;  // float32 plans: v arranged the same way
   const c* tlo;   // inter-pass twiddles (KIND_COL)
   const c* thi;
   Geo geo;
@@ -432,13 +513,32 @@ template <class K, class F> __device__ __forceinline__ void for_slot_segments(in
 // (S x NS values), copied asynchronously one transaction ahead; the stage of
 // the current transaction then serves as its exchange buffer and as the
 // scratch of the checksum-group reduction.
-constexpr int NSTAGE = 2;
+#ifndef TF_NSTAGE
+#define TF_NSTAGE 2
+#endif
+constexpr int NSTAGE = TF_NSTAGE;
 template <class K> constexpr int stage_bytes() {
-  constexpr int red = Seg<K>::COUNT * 64 + K::S * 4;
+  constexpr int red = Seg<K>::COUNT * 64 + (K::S + 1) * 4;  // partial sums, slot flags, "any" flag
   constexpr int b = (K::SMEM_BYTES > red) ? K::SMEM_BYTES : red;
   return (b + 127) / 128 * 128;
 }
-template <class K> constexpr int pass_smem_bytes() { return NSTAGE * stage_bytes<K>(); }
+// checksum vectors e and v staged in shared memory once per block when
+// they are small (read once per element per transaction)
+// Optionally (TF_PAIRED_CHECKSUMS) float32 checksums use paired FP32 FMAs
+// (FFMA2) with the weights arranged as (re, re, im, im); the column pass
+// weights e by the inter-pass twiddle per element and keeps the scalar form
+template <class K> constexpr bool paired_ft() {
+#ifdef TF_PAIRED_CHECKSUMS
+  return sizeof(typename K::real) == 4;
+#else
+  return false;  // measured slower on GB300: the 16-byte weights double the shared-memory traffic
+#endif
+}
+template <class K> constexpr int ev_entry_bytes() { return paired_ft<K>() ? 16 : (int)sizeof(typename K::c); }
+template <class K> constexpr bool ev_in_smem() { return 2 * K::NS * ev_entry_bytes<K>() <= 32768; }
+template <class K, int FTM = 0> constexpr int pass_smem_bytes() {
+  return NSTAGE * stage_bytes<K>() + ((FTM != 0 && ev_in_smem<K>()) ? 2 * K::NS * ev_entry_bytes<K>() : 0);
+}
 
 // ---------------------------------------------------------------------------
 // asynchronous global -> shared copies (cp.async, 16 bytes, L2 only)
@@ -503,7 +603,8 @@ __device__ __forceinline__ void atomic_max_nonneg(float* addr, float v) {
 // path from HBM; 2 = checksums, right-side sums kept in registers during the
 // pass (the thread-level accumulation of Sec. 4.3)
 template <class K, int FTM>
-__global__ void __launch_bounds__(K::NT, K::MINB) tf_pass_kernel(const PassArgs<typename K::real> A) {
+__global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_FT : TwMode<K>::MINB)
+    tf_pass_kernel(const PassArgs<typename K::real> A) {
   using R = typename K::real;
   using c = typename K::c;
   constexpr int E = K::E, P = K::P, S = K::S;
@@ -517,6 +618,35 @@ __global__ void __launch_bounds__(K::NT, K::MINB) tf_pass_kernel(const PassArgs<
   const int t = K::SLOT_FAST ? (tid / S) : (tid % P);
   const Geo g = A.geo;
   const long long stride = gridDim.x;
+  TwReg<K, FT ? TF_FT_TW_BUDGET : 64> twr;
+  twr.load(A.tw, t);
+  // checksum vectors: shared-memory copies (small NS) or the global tables
+  const c* __restrict__ evp = A.ev;
+  const c* __restrict__ vvp = A.vv;
+  const float4* __restrict__ ev4p = A.ev4;
+  const float4* __restrict__ vv4p = A.vv4;
+  if constexpr (FT && ev_in_smem<K>()) {
+    if constexpr (paired_ft<K>()) {
+      float4* evs = reinterpret_cast<float4*>(smem_raw + NSTAGE * stage_bytes<K>());
+      float4* vvs = evs + K::NS;
+      for (int q = tid; q < K::NS; q += K::NT) {
+        evs[q] = A.ev4[q];
+        vvs[q] = A.vv4[q];
+      }
+      ev4p = evs;
+      vv4p = vvs;
+    } else {
+      c* evs = reinterpret_cast<c*>(smem_raw + NSTAGE * stage_bytes<K>());
+      c* vvs = evs + K::NS;
+      for (int q = tid; q < K::NS; q += K::NT) {
+        evs[q] = A.ev[q];
+        vvs[q] = A.vv[q];
+      }
+      evp = evs;
+      vvp = vvs;
+    }
+    __syncthreads();
+  }
 
   // checksum-group state (per thread)
   c xs[EAGER ? E : 1], ys[EAGER ? E : 1];
@@ -525,7 +655,8 @@ __global__ void __launch_bounds__(K::NT, K::MINB) tf_pass_kernel(const PassArgs<
   int gi = 0;                     // transaction index inside the group
   long long g_unit0 = blockIdx.x;
   long long groups = 0;
-  float max_ratio = 0.f;
+  float max_ratio2 = 0.f;  // max (|S1| / tau)^2 over clean groups
+  const R tau_coef2 = (R)(A.tau_coef * A.tau_coef);
   if constexpr (EAGER) {
 #pragma unroll
     for (int i = 0; i < E; ++i) { xs[i] = mk<c>(0, 0); ys[i] = mk<c>(0, 0); }
@@ -565,11 +696,27 @@ __global__ void __launch_bounds__(K::NT, K::MINB) tf_pass_kernel(const PassArgs<
     // ---- input side of the checksums
     c pin = mk<c>(0, 0);
     if constexpr (FT) {
+      if constexpr (paired_ft<K>()) {
+        // (sum v.re x, sum v.im x) with x = (re, im): two FFMA2 per element
+        float2 q1 = make_float2(0.f, 0.f), q2 = make_float2(0.f, 0.f), e2 = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int i = 0; i < E; ++i) {
-        if constexpr (EAGER) xs[i] = cadd(xs[i], a[i]);
-        cmac(pin, ldg(A.vv + t + i * P), a[i]);
-        en += a[i].x * a[i].x + a[i].y * a[i].y;
+        for (int i = 0; i < E; ++i) {
+          if constexpr (EAGER) xs[i] = cadd(xs[i], a[i]);
+          const float4 w = vv4p[t + i * P];
+          q1 = __ffma2_rn(make_float2(w.x, w.y), a[i], q1);
+          q2 = __ffma2_rn(make_float2(w.z, w.w), a[i], q2);
+          e2 = __ffma2_rn(a[i], a[i], e2);
+        }
+        pin = mk<c>(q1.x - q2.y, q1.y + q2.x);
+        en += e2.x + e2.y;
+      } else {
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+          if constexpr (EAGER) xs[i] = cadd(xs[i], a[i]);
+          cmac(pin, vvp[t + i * P], a[i]);
+          en = fma(a[i].x, a[i].x, en);
+          en = fma(a[i].y, a[i].y, en);
+        }
       }
     }
     // ---- injection context (armed one-shot site)
@@ -582,21 +729,33 @@ __global__ void __launch_bounds__(K::NT, K::MINB) tf_pass_kernel(const PassArgs<
       ic.bit = A.inj.bit;
     }
     // ---- the radix passes
-    Passes<K, 0>::run(a, sm, A.tw, slot, t, ic);
+    Passes<K, 0>::run(a, sm, twr, slot, t, ic);
     // ---- inter-pass twiddle (four-step, first pass), output side of checksums
     c pout = mk<c>(0, 0);
+    if constexpr (K::KIND == KIND_COL || !paired_ft<K>()) {
 #pragma unroll
-    for (int i = 0; i < E; ++i) {
-      const int pos = t + i * P;
-      if constexpr (K::KIND == KIND_COL) {
-        const c w = colTwiddle<K>(g, A.tlo, A.thi, valid ? sig : 0, pos);
-        if constexpr (EAGER) ys[i] = cadd(ys[i], a[i]);
-        a[i] = cmul(a[i], w);
-        if constexpr (FT) cmac(pout, cmul(ldg(A.ev + pos), cconj(w)), a[i]);
-      } else {
-        if constexpr (EAGER) ys[i] = cadd(ys[i], a[i]);
-        if constexpr (FT) cmac(pout, ldg(A.ev + pos), a[i]);
+      for (int i = 0; i < E; ++i) {
+        const int pos = t + i * P;
+        if constexpr (K::KIND == KIND_COL) {
+          const c w = colTwiddle<K>(g, A.tlo, A.thi, valid ? sig : 0, pos);
+          if constexpr (EAGER) ys[i] = cadd(ys[i], a[i]);
+          a[i] = cmul(a[i], w);
+          if constexpr (FT) cmac(pout, cmul(evp[pos], cconj(w)), a[i]);
+        } else {
+          if constexpr (EAGER) ys[i] = cadd(ys[i], a[i]);
+          if constexpr (FT) cmac(pout, evp[pos], a[i]);
+        }
       }
+    } else if constexpr (FT) {
+      float2 q1 = make_float2(0.f, 0.f), q2 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        if constexpr (EAGER) ys[i] = cadd(ys[i], a[i]);
+        const float4 w = ev4p[t + i * P];
+        q1 = __ffma2_rn(make_float2(w.x, w.y), a[i], q1);
+        q2 = __ffma2_rn(make_float2(w.z, w.w), a[i], q2);
+      }
+      pout = mk<c>(q1.x - q2.y, q1.y + q2.x);
     }
     // ---- store
     if constexpr (K::KIND == KIND_ROW) {
@@ -643,74 +802,116 @@ __global__ void __launch_bounds__(K::NT, K::MINB) tf_pass_kernel(const PassArgs<
     const bool group_end = (gi == A.T) || (unit + stride >= A.num_units);
     if constexpr (FT) {
       if (group_end) {
-        // ---- reduce the group over the threads of each slot
+        // ---- reduce the group over the threads of each slot.  Phase 1
+        // reduces S1 and the energy in the working precision and clears
+        // every slot whose |S1|^2 is below tau^2 / 2 (far more margin than
+        // the rounding of that sum); only if some slot is not clearly clean
+        // does phase 2 redo the reduction of S1, S2, the energy and the
+        // non-finite markers in float64 and take the decision there.
         __syncthreads();  // the exchange buffer is free now
-        double* red = reinterpret_cast<double*>(sm);
+        R* redr = reinterpret_cast<R*>(sm);
         int* flag = reinterpret_cast<int*>(reinterpret_cast<char*>(sm) + (size_t)Seg<K>::COUNT * 8 * sizeof(double));
-        R v0 = seg_reduce_sum<K>(s1r), v1 = seg_reduce_sum<K>(s1i);
-        R v2 = seg_reduce_sum<K>(s2r), v3 = seg_reduce_sum<K>(s2i);
-        R v4 = seg_reduce_sum<K>(en);
-        int blo = seg_reduce_min<K>(bad_lo), bhi = seg_reduce_max<K>(bad_hi);
-        int seg;
-        if (seg_leader<K>(tid, seg)) {
-          double* d = red + seg * 8;
-          d[0] = (double)v0; d[1] = (double)v1; d[2] = (double)v2; d[3] = (double)v3; d[4] = (double)v4;
-          d[5] = (double)blo; d[6] = (double)bhi;
+        int* anyflag = flag + S;
+        if (tid == 0) *anyflag = 0;
+        {
+          const R v0 = seg_reduce_sum<K>(s1r), v1 = seg_reduce_sum<K>(s1i), v4 = seg_reduce_sum<K>(en);
+          int seg;
+          if (seg_leader<K>(tid, seg)) {
+            redr[seg * 4 + 0] = v0;
+            redr[seg * 4 + 1] = v1;
+            redr[seg * 4 + 2] = v4;
+          }
         }
         __syncthreads();
         if (tid < S) {
-          double S1r = 0, S1i = 0, S2r = 0, S2i = 0, EN = 0;
-          int lo = 0x7fffffff, hi = -1;
+          R S1r = 0, S1i = 0, EN = 0;
           for_slot_segments<K>(tid, [&](int sgi) {
-            const double* d = red + sgi * 8;
-            S1r += d[0]; S1i += d[1]; S2r += d[2]; S2i += d[3]; EN += d[4];
-            lo = min(lo, (int)d[5]); hi = max(hi, (int)d[6]);
+            S1r += redr[sgi * 4 + 0];
+            S1i += redr[sgi * 4 + 1];
+            EN += redr[sgi * 4 + 2];
           });
-          const double tau = A.tau_coef * sqrt((double)K::NS * EN);
-          const double mag = sqrt(S1r * S1r + S1i * S1i);
-          const bool finite = isfinite(S1r) && isfinite(S1i) && isfinite(EN);
-          int rec = -1;
-          // a slot with no valid signal in this group has EN == 0 and S1 == 0
-          if (finite && mag <= tau) {
-            if (tau > 0) max_ratio = fmaxf(max_ratio, (float)(mag / tau));
+          const R tau2 = tau_coef2 * (R)K::NS * EN;
+          const R mag2 = S1r * S1r + S1i * S1i;
+          if (isfinite(mag2) && isfinite(tau2) && mag2 <= (R)0.5 * tau2) {
+            if (tau2 > 0) max_ratio2 = fmaxf(max_ratio2, (float)(mag2 / tau2));
           } else {
-            int located = -1;
-            if (hi >= 0) {
-              located = (lo == hi) ? lo : -2;   // non-finite residuals: direct location
-            } else if (finite) {
-              const double den = S1r * S1r + S1i * S1i;
-              const double qr = (S2r * S1r + S2i * S1i) / den, qi = (S2i * S1r - S2r * S1i) / den;
-              const double kk = floor(qr + 0.5);
-              if (isfinite(qr) && isfinite(qi) && kk >= 1 && kk <= gi &&
-                  sqrt((qr - kk) * (qr - kk) + qi * qi) < 0.25)
-                located = (int)kk - 1;
-            }
-            atomicAdd(&A.fts->detected, 1ull);
-            unsigned long long r = atomicAdd(&A.fts->num_records, 1ull);
-            if (r < (unsigned long long)MAX_RECORDS) {
-              FtRecord& R0 = A.fts->rec[r];
-              R0.pass_id = A.pass_id;
-              R0.slot = tid;
-              R0.count = gi;
-              R0.located = located;
-              R0.unit0 = g_unit0;
-              R0.unit_stride = stride;
-              R0.transform_base = A.transform_base;
-              R0.s1r = S1r; R0.s1i = S1i; R0.s2r = S2r; R0.s2i = S2i;
-              R0.tau = tau;
-              R0.energy = EN;
-              R0.result = FT_RES_PENDING;
-              R0.has_sums = EAGER ? 1 : 0;
-              R0.signal = -1;
-              rec = (int)r;
-            } else {
-              atomicAdd(&A.fts->dropped, 1ull);
-            }
+            *anyflag = 1;
           }
-          flag[tid] = rec;
         }
         __syncthreads();
+        const bool check = *anyflag != 0;
+        if (check) {
+          // phase 2 (rare): float64 decision, location, record
+          __syncthreads();
+          double* red = reinterpret_cast<double*>(sm);
+          R v0 = seg_reduce_sum<K>(s1r), v1 = seg_reduce_sum<K>(s1i);
+          R v2 = seg_reduce_sum<K>(s2r), v3 = seg_reduce_sum<K>(s2i);
+          R v4 = seg_reduce_sum<K>(en);
+          int blo = seg_reduce_min<K>(bad_lo), bhi = seg_reduce_max<K>(bad_hi);
+          int seg;
+          if (seg_leader<K>(tid, seg)) {
+            double* d = red + seg * 8;
+            d[0] = (double)v0; d[1] = (double)v1; d[2] = (double)v2; d[3] = (double)v3; d[4] = (double)v4;
+            d[5] = (double)blo; d[6] = (double)bhi;
+          }
+          __syncthreads();
+          if (tid < S) {
+            double S1r = 0, S1i = 0, S2r = 0, S2i = 0, EN = 0;
+            int lo = 0x7fffffff, hi = -1;
+            for_slot_segments<K>(tid, [&](int sgi) {
+              const double* d = red + sgi * 8;
+              S1r += d[0]; S1i += d[1]; S2r += d[2]; S2i += d[3]; EN += d[4];
+              lo = min(lo, (int)d[5]); hi = max(hi, (int)d[6]);
+            });
+            const double tau = A.tau_coef * sqrt((double)K::NS * EN);
+            const double mag = sqrt(S1r * S1r + S1i * S1i);
+            const bool finite = isfinite(S1r) && isfinite(S1i) && isfinite(EN);
+            int rec = -1;
+            // a slot with no valid signal in this group has EN == 0 and S1 == 0
+            if (finite && mag <= tau) {
+              if (tau > 0) max_ratio2 = fmaxf(max_ratio2, (float)((mag / tau) * (mag / tau)));
+            } else {
+              int located = -1;
+              if (hi >= 0) {
+                located = (lo == hi) ? lo : -2;   // non-finite residuals: direct location
+              } else if (finite) {
+                const double den = S1r * S1r + S1i * S1i;
+                const double qr = (S2r * S1r + S2i * S1i) / den, qi = (S2i * S1r - S2r * S1i) / den;
+                const double kk = floor(qr + 0.5);
+                if (isfinite(qr) && isfinite(qi) && kk >= 1 && kk <= gi &&
+                    sqrt((qr - kk) * (qr - kk) + qi * qi) < 0.25)
+                  located = (int)kk - 1;
+              }
+              atomicAdd(&A.fts->detected, 1ull);
+              unsigned long long r = atomicAdd(&A.fts->num_records, 1ull);
+              if (r < (unsigned long long)MAX_RECORDS) {
+                FtRecord& R0 = A.fts->rec[r];
+                R0.pass_id = A.pass_id;
+                R0.slot = tid;
+                R0.count = gi;
+                R0.located = located;
+                R0.unit0 = g_unit0;
+                R0.unit_stride = stride;
+                R0.transform_base = A.transform_base;
+                R0.s1r = S1r; R0.s1i = S1i; R0.s2r = S2r; R0.s2i = S2i;
+                R0.tau = tau;
+                R0.energy = EN;
+                R0.result = FT_RES_PENDING;
+                R0.has_sums = EAGER ? 1 : 0;
+                R0.signal = -1;
+                rec = (int)r;
+              } else {
+                atomicAdd(&A.fts->dropped, 1ull);
+              }
+            }
+            flag[tid] = rec;
+          }
+          __syncthreads();
+        } else if (tid < S) {
+          flag[tid] = -1;
+        }
         if constexpr (EAGER) {
+          __syncthreads();
           const int myrec = flag[slot];
           if (myrec >= 0) {
             // right-side sums of this slot -> the record, for delayed correction
@@ -736,7 +937,7 @@ __global__ void __launch_bounds__(K::NT, K::MINB) tf_pass_kernel(const PassArgs<
   }
   if constexpr (FT) {
     if (tid == 0 && groups > 0) atomicAdd(&A.fts->groups, (unsigned long long)(groups * S));
-    if (tid < S && max_ratio > 0.f) atomic_max_nonneg(&A.fts->max_clean_ratio, max_ratio);
+    if (tid < S && max_ratio2 > 0.f) atomic_max_nonneg(&A.fts->max_clean_ratio, sqrtf(max_ratio2));
   }
 }
 
@@ -915,7 +1116,9 @@ __global__ void __launch_bounds__(K::NT) tf_fix_kernel(const PassArgs<typename K
           for (int i = 0; i < E; ++i) { a[i] = cadd(a[i], xv[i]); yb[i] = cadd(yb[i], yv[i]); }
         }
       }
-      fft_block<K>(a, sm, A.tw, slot, t);
+      TwReg<K> twr;
+      twr.load(A.tw, t);
+      fft_block<K>(a, sm, twr, slot, t);
       c cand[E];
       bool fin = true;
 #pragma unroll
@@ -939,7 +1142,9 @@ __global__ void __launch_bounds__(K::NT) tf_fix_kernel(const PassArgs<typename K
       c a[E];
 #pragma unroll
       for (int i = 0; i < E; ++i) a[i] = x[i];
-      fft_block<K>(a, sm, A.tw, slot, t);
+      TwReg<K> twr;
+      twr.load(A.tw, t);
+      fft_block<K>(a, sm, twr, slot, t);
       double rr, ri, e2;
       residual<K>(A, red, slot, t, x, a, rr, ri, e2);
       if (sqrt(rr * rr + ri * ri) <= tau_k) {

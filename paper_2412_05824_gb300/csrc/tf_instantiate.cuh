@@ -7,7 +7,7 @@
 namespace tf {
 
 template <class K, int FTM> void launch_main(const void* a, int grid, cudaStream_t s) {
-  tf_pass_kernel<K, FTM><<<grid, K::NT, pass_smem_bytes<K>(), s>>>(
+  tf_pass_kernel<K, FTM><<<grid, K::NT, pass_smem_bytes<K, FTM>(), s>>>(
       *static_cast<const PassArgs<typename K::real>*>(a));
 }
 template <class K> void launch_fix(const void* a, int grid, cudaStream_t s) {
@@ -23,7 +23,9 @@ template <class K> KernelEntry make_entry() {
   e.s = K::S;
   e.nt = K::NT;
   e.stages = K::NP;
-  e.smem_main = pass_smem_bytes<K>();
+  e.smem_main[0] = pass_smem_bytes<K, 0>();
+  e.smem_main[1] = pass_smem_bytes<K, 1>();
+  e.smem_main[2] = pass_smem_bytes<K, 2>();
   e.smem_fix = K::SMEM_BYTES;
   e.main[0] = &launch_main<K, 0>;
   e.main[1] = &launch_main<K, 1>;

@@ -15,7 +15,7 @@ struct KernelEntry {
   int s;            // sub-transforms per transaction
   int nt;           // threads per block
   int stages;       // radix passes
-  int smem_main;    // dynamic shared memory of the transform kernel
+  int smem_main[3]; // dynamic shared memory of the transform kernel per variant
   int smem_fix;     // dynamic shared memory of the correction kernel
   LaunchFn main[3];   // transform kernel: no checksums / checksums / checksums + register sums
   LaunchFn fix;       // correction kernel
