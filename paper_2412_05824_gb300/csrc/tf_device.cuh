@@ -68,6 +68,33 @@ template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 template <typename C> __device__ __forceinline__ C cconj(C a) { return mk<C>(a.x, -a.y); }
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C cmulconj(C a, C b) {
+  return mk<C>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+// conjugation as an integer sign flip of the imaginary part under a mask
+// (0 or the sign bit), so that no floating-point pipe is used for it
+__device__ __forceinline__ float2 conj_mask(float2 v, unsigned long long m) {
+  return make_float2(v.x, __uint_as_float(__float_as_uint(v.y) ^ (unsigned)m));
+}
+__device__ __forceinline__ double2 conj_mask(double2 v, unsigned long long m) {
+  return make_double2(v.x, __longlong_as_double(__double_as_longlong(v.y) ^ (long long)m));
+}
+// |v| of a double as a float built with integer operations from its
+// exponent and top 20 mantissa bits (relative error < 2^-20): for the energy
+// that only scales the checksum threshold.  Exponents below the float range
+// give 0 or a subnormal, above it the float exponent 254 (the caller checks
+// the sum for overflow and falls back to float64).
+__device__ __forceinline__ float abs_as_float(double v) {
+  const int hi = __double2hiint(v);
+  int fe = ((hi >> 20) & 0x7FF) - 1023 + 127;
+  fe = fe < 0 ? 0 : (fe > 254 ? 254 : fe);
+  return __uint_as_float(((unsigned)fe << 23) | (((unsigned)hi & 0xFFFFFu) << 3));
+}
+
+template <typename C> __device__ __forceinline__ unsigned long long sign_mask(int on) {
+  return on ? (sizeof(decltype(C::x)) == 4 ? 0x80000000ull : 0x8000000000000000ull) : 0ull;
+}
 template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return mk<C>(a.x * s, a.y * s); }
 // acc += a*b as four chained fused multiply-adds
 template <typename C> __device__ __forceinline__ void cmac(C& acc, C a, C b) {
@@ -620,6 +647,8 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
   const long long stride = gridDim.x;
   TwReg<K, FT ? TF_FT_TW_BUDGET : 64> twr;
   twr.load(A.tw, t);
+  const unsigned long long mask_in = sign_mask<c>(A.conj_in), mask_out = sign_mask<c>(A.conj_out);
+  const bool scaled = A.out_scale != (R)1;
   // checksum vectors: shared-memory copies (small NS) or the global tables
   const c* __restrict__ evp = A.ev;
   const c* __restrict__ vvp = A.vv;
@@ -690,7 +719,7 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
       c v = mk<c>(0, 0);
       const int pos = t + i * P;
       if (valid) v = K::SLOT_FAST ? sm[pos * S + slot] : sm[slot * K::NS + pos];
-      a[i] = A.conj_in ? cconj(v) : v;
+      a[i] = conj_mask(v, mask_in);
     }
     __syncthreads();  // the tile is consumed; the stage becomes the exchange buffer
     // ---- input side of the checksums
@@ -709,6 +738,29 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
         }
         pin = mk<c>(q1.x - q2.y, q1.y + q2.x);
         en += e2.x + e2.y;
+      } else if constexpr (sizeof(R) == 8) {
+        // float64: the energy only scales tau, so it is accumulated in
+        // float32 from converted values, keeping the float64 pipe for the
+        // transform and the checksum products
+        float enf = 0.f;
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+          if constexpr (EAGER) xs[i] = cadd(xs[i], a[i]);
+          cmac(pin, vvp[t + i * P], a[i]);
+          const float fx = abs_as_float(a[i].x), fy = abs_as_float(a[i].y);
+          enf = fmaf(fx, fx, enf);
+          enf = fmaf(fy, fy, enf);
+        }
+        if (isfinite(enf)) {
+          en += (R)enf;
+        } else {
+          // values beyond the float32 range: the exact energy (rare)
+#pragma unroll
+          for (int i = 0; i < E; ++i) {
+            en = fma(a[i].x, a[i].x, en);
+            en = fma(a[i].y, a[i].y, en);
+          }
+        }
       } else {
 #pragma unroll
         for (int i = 0; i < E; ++i) {
@@ -740,7 +792,7 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
           const c w = colTwiddle<K>(g, A.tlo, A.thi, valid ? sig : 0, pos);
           if constexpr (EAGER) ys[i] = cadd(ys[i], a[i]);
           a[i] = cmul(a[i], w);
-          if constexpr (FT) cmac(pout, cmul(evp[pos], cconj(w)), a[i]);
+          if constexpr (FT) cmac(pout, cmulconj(evp[pos], w), a[i]);
         } else {
           if constexpr (EAGER) ys[i] = cadd(ys[i], a[i]);
           if constexpr (FT) cmac(pout, evp[pos], a[i]);
@@ -757,7 +809,11 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
       }
       pout = mk<c>(q1.x - q2.y, q1.y + q2.x);
     }
-    // ---- store
+    // ---- store (scaled inverse: one uniform branch around the scaling)
+    if (scaled) {
+#pragma unroll
+      for (int i = 0; i < E; ++i) a[i] = cscale(a[i], A.out_scale);
+    }
     if constexpr (K::KIND == KIND_ROW) {
       // transposed store: rows r0..r0+S-1 are contiguous in the output for a
       // fixed k2, so go through shared memory and store slot-fast
@@ -769,9 +825,7 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         const int pos = t2 + i * P;
-        c v = sm[s2 * K::NS + (pos ^ (s2 & ((1 << K::B) - 1)))];
-        if (A.conj_out) v = cconj(v);
-        v = cscale(v, A.out_scale);
+        const c v = conj_mask(sm[s2 * K::NS + (pos ^ (s2 & ((1 << K::B) - 1)))], mask_out);
         __stcs(A.out + out_off<K>(g, sig2, pos), v);  // streaming: keep L1 for the tables
       }
       __syncthreads();
@@ -779,9 +833,7 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
       if (valid) {
 #pragma unroll
         for (int i = 0; i < E; ++i) {
-          c v = a[i];
-          if (A.conj_out) v = cconj(v);
-          v = cscale(v, A.out_scale);
+          const c v = conj_mask(a[i], mask_out);
           __stcs(A.out + out_off<K>(g, sig, t + i * P), v);
         }
       }
