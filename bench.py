@@ -141,6 +141,37 @@ def ncu_traffic(key):
 
 
 # ---------------------------------------------------------------------------
+# multi-rank plumbing: one process per GPU, each rank a replica with its own
+# seeded data (transforms are independent; no data-path collective)
+# ---------------------------------------------------------------------------
+def dist_env():
+    """(world, rank, local_rank) from the torch.distributed.run environment."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def rank_seed(rank: int) -> int:
+    """Seed of a rank's synthetic input: distinct data on every replica."""
+    return 2 + 1000 * rank
+
+
+def max_over_ranks(v: float, world: int, device=None) -> float:
+    """Largest value over the ranks (the slowest rank's time)."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_gbs(bytes_per_rank_step: float, steps: int, max_ms: float, world: int) -> float:
+    """Whole-job throughput: bytes moved by all ranks over the slowest rank's time."""
+    return world * bytes_per_rank_step * steps / (max_ms * 1e-3) / 1e9
+
+
+# ---------------------------------------------------------------------------
 # the CPU oracle on a bounded sample (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
 def oracle_sample(args, sample_elems=1 << 22):
@@ -162,7 +193,7 @@ def oracle_sample(args, sample_elems=1 << 22):
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
+    world, rank, _ = dist_env()
     if rank != 0:
         return
     import oracle
@@ -200,9 +231,7 @@ def run_ours(args):
     import paper_2412_05824_gb300 as tfl
     import synth_signals as ss
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = dist_env()
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -218,7 +247,7 @@ def run_ours(args):
     # inputs resident in HBM (seeded, per rank), one buffer per dtype
     bufs = {}
     for dt, eb in DTYPES:
-        x = ss.uniform_complex_torch(2 + 1000 * rank, 1, ELEMENTS, dt, device=dev)
+        x = ss.uniform_complex_torch(rank_seed(rank), 1, ELEMENTS, dt, device=dev)
         bufs[dt] = (x, torch.empty_like(x))
     workspace = torch.empty(ELEMENTS, dtype=torch.complex128, device=dev)  # two-pass intermediate
 
@@ -279,17 +308,10 @@ def run_ours(args):
     # fault-tolerance outcome of the last exec of every plan: a clean run
     fa = sum(plans_ft[(dt, d, n)].report()["detected"] for dt, eb, d, n in cfgs)
 
-    def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    ms_ft = max_over_ranks(ms_ft)
-    ms_plain = max_over_ranks(ms_plain)
-    value = world * step_bytes * args.steps / (ms_ft * 1e-3) / 1e9
-    value_plain = world * step_bytes * args.steps / (ms_plain * 1e-3) / 1e9
+    ms_ft = max_over_ranks(ms_ft, world, dev)
+    ms_plain = max_over_ranks(ms_plain, world, dev)
+    value = aggregate_gbs(step_bytes, args.steps, ms_ft, world)
+    value_plain = aggregate_gbs(step_bytes, args.steps, ms_plain, world)
 
     # dominant kernel: the kernel with the largest share of one profiled step
     # (CUDA events on the exec's stream around every launch), then its
@@ -353,7 +375,7 @@ def run_ours(args):
                 hx, hy = host[dt2]
                 plans_ft[(dt2, d2, n2)].exec_host(hx, hy)
         barrier()
-        el = max_over_ranks(time.perf_counter() - t0)
+        el = max_over_ranks(time.perf_counter() - t0, world, dev)
         h2d = sum(ELEMENTS * eb2 for dt2, eb2, d2, n2 in cfgs)
         e2e = {"value": round(world * step_bytes * args.steps / el / 1e9, 2), "unit": "GB/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
