@@ -68,6 +68,7 @@ typedef enum {
 #define TURBOFFT_FORWARD (-1)          /* y = W x,            W = (w^{jk}), w = e^{-2 pi i/N} */
 #define TURBOFFT_INVERSE (1)           /* y = (1/N) conj(W) x  (Sec. 2.2.1 inverse) */
 #define TURBOFFT_INVERSE_UNSCALED (2)  /* y = conj(W) x = W^H x, the adjoint of FORWARD */
+#define TURBOFFT_FORWARD_SCALED (-2)   /* y = (1/N) W x, the adjoint of INVERSE */
 
 typedef enum {
   TURBOFFT_FT_OFF = 0,            /* plain FFT, no checksums */
@@ -149,7 +150,8 @@ typedef struct {
  *   n          transform length, a power of two in [8, 2^24]
  *   batch      number of transforms, >= 1, batch * n <= 2^31 elements
  *   dtype      TURBOFFT_C2C_F32 or TURBOFFT_C2C_F64
- *   direction  TURBOFFT_FORWARD, TURBOFFT_INVERSE or TURBOFFT_INVERSE_UNSCALED
+ *   direction  TURBOFFT_FORWARD, TURBOFFT_INVERSE, TURBOFFT_INVERSE_UNSCALED or
+ *              TURBOFFT_FORWARD_SCALED
  *   ft_mode    TURBOFFT_FT_OFF / _DETECT / _CORRECT
  *   plan       out: the new plan (set to NULL on failure)
  * Tables (twiddles, checksum vectors e and e^T W) are computed on the host

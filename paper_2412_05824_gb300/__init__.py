@@ -32,13 +32,15 @@ C2C_F64 = 1
 FORWARD = -1
 INVERSE = 1
 INVERSE_UNSCALED = 2
+FORWARD_SCALED = -2
 FT_OFF = 0
 FT_DETECT = 1
 FT_CORRECT = 2
 FT_CORRECT_REGISTERS = 3
 
 _DIRS = {"forward": FORWARD, "inverse": INVERSE, "inverse_unscaled": INVERSE_UNSCALED,
-         FORWARD: FORWARD, INVERSE: INVERSE, INVERSE_UNSCALED: INVERSE_UNSCALED}
+         "forward_scaled": FORWARD_SCALED, FORWARD: FORWARD, INVERSE: INVERSE,
+         INVERSE_UNSCALED: INVERSE_UNSCALED, FORWARD_SCALED: FORWARD_SCALED}
 _FT = {"off": FT_OFF, "detect": FT_DETECT, "correct": FT_CORRECT, "correct_registers": FT_CORRECT_REGISTERS,
        None: FT_OFF, False: FT_OFF, FT_OFF: FT_OFF, FT_DETECT: FT_DETECT, FT_CORRECT: FT_CORRECT,
        FT_CORRECT_REGISTERS: FT_CORRECT_REGISTERS}

@@ -291,11 +291,12 @@ void fill_args(const turbofft_plan* p, int pi, const void* in, void* out, int64_
   A.geo.n2 = p->n2;
   A.geo.batch = batch;
   A.num_units = units_for(p, pi, batch);
-  const bool inverse = p->direction != TURBOFFT_FORWARD;
+  const bool inverse = p->direction > 0;
+  const bool scaled = p->direction == TURBOFFT_INVERSE || p->direction == TURBOFFT_FORWARD_SCALED;
   const bool last = (pi == p->num_passes - 1);
   A.conj_in = (inverse && pi == 0) ? 1 : 0;
   A.conj_out = (inverse && last) ? 1 : 0;
-  A.out_scale = (last && p->direction == TURBOFFT_INVERSE) ? (R)(1.0 / (double)p->n) : (R)1;
+  A.out_scale = (last && scaled) ? (R)(1.0 / (double)p->n) : (R)1;
   A.tau_coef = pp.tau_coef * p->threshold_scale;
   A.ft = p->ft_mode == TURBOFFT_FT_CORRECT_REGISTERS ? TURBOFFT_FT_CORRECT : p->ft_mode;
   A.T = p->T;
@@ -433,7 +434,8 @@ turbofft_status turbofft_plan_create(int64_t n, int64_t batch, turbofft_dtype dt
   if (logn < 3 || logn > 24) return TURBOFFT_INVALID_VALUE;
   if (batch < 1 || batch * n > ((int64_t)1 << 31)) return TURBOFFT_INVALID_VALUE;
   if (dtype != TURBOFFT_C2C_F32 && dtype != TURBOFFT_C2C_F64) return TURBOFFT_INVALID_VALUE;
-  if (direction != TURBOFFT_FORWARD && direction != TURBOFFT_INVERSE && direction != TURBOFFT_INVERSE_UNSCALED)
+  if (direction != TURBOFFT_FORWARD && direction != TURBOFFT_INVERSE && direction != TURBOFFT_INVERSE_UNSCALED &&
+      direction != TURBOFFT_FORWARD_SCALED)
     return TURBOFFT_INVALID_VALUE;
   if (ft_mode != TURBOFFT_FT_OFF && ft_mode != TURBOFFT_FT_DETECT && ft_mode != TURBOFFT_FT_CORRECT &&
       ft_mode != TURBOFFT_FT_CORRECT_REGISTERS)
