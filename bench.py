@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--sizes", default="", help="comma list of log2 N (default: the full sweep)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-ragged", action="store_true", help="skip the ragged-batch comparison")
+    ap.add_argument("--no-filter", action="store_true", help="skip the spectral-filter comparison")
     return ap.parse_args()
 
 
@@ -222,6 +224,192 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# secondary workloads: ragged batch and differentiable spectral filter, each
+# against the plain fixed-size form on the same GPU
+# ---------------------------------------------------------------------------
+RAGGED_COUNT, RAGGED_LOG_LO, RAGGED_LOG_HI, RAGGED_SEED = 20000, 6, 16, 2024
+
+
+def time_calls(fn, warmup, reps, stream):
+    """Mean ms of fn() over `reps` calls (CUDA events on `stream`)."""
+    import torch
+    for _ in range(max(3, warmup)):
+        fn()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(reps):
+        fn()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1) / reps
+
+
+def bench_ragged(args, dev, stream, rank, peaks):
+    """20,000 complex64 transforms, sizes log-uniform in 2^6..2^16 (seeded),
+    packed back to back: ragged plan (one CUDA graph, autotuned shapes, ABFT
+    on) against one plain launch per size on the same transforms laid out
+    contiguously by size."""
+    import numpy as np
+    import torch
+
+    import paper_2412_05824_gb300 as tfl
+    import synth_signals as ss
+
+    sizes = ss.ragged_sizes(RAGGED_SEED, RAGGED_COUNT, RAGGED_LOG_LO, RAGGED_LOG_HI)
+    offsets, extent = ss.ragged_offsets(sizes)
+    x = ss.uniform_complex_torch(rank_seed(rank) + 100, 1, extent, "float32", device=dev).view(-1)
+    y = torch.empty_like(x)
+    tfl.set_autotune(True)
+    t0 = time.perf_counter()
+    rag = {"correct": tfl.RaggedPlan(sizes, offsets, "complex64", "forward", "correct"),
+           "off": tfl.RaggedPlan(sizes, offsets, "complex64", "forward", "off")}
+    tune_s = time.perf_counter() - t0
+    tfl.set_autotune(False)
+    rag_default = tfl.RaggedPlan(sizes, offsets, "complex64", "forward", "correct")
+
+    # the same transforms, contiguous per size (gathered once on the device)
+    order = np.argsort(sizes, kind="stable")
+    ssz = sizes[order]
+    starts_sorted = np.concatenate([[0], np.cumsum(ssz)[:-1]])
+    delta = torch.from_numpy(offsets[order] - starts_sorted).to(dev)
+    idx = torch.repeat_interleave(delta, torch.from_numpy(ssz).to(dev)) + torch.arange(extent, device=dev)
+    xs = x[idx]
+    ys = torch.empty_like(xs)
+    groups = []
+    for n in np.unique(ssz):
+        first = int(np.searchsorted(ssz, n))
+        cnt = int(np.sum(ssz == n))
+        groups.append((int(n), cnt, int(starts_sorted[first])))
+    per = {ft: [(tfl.Plan(n, c, "complex64", "forward", ft), o) for n, c, o in groups] for ft in ("off", "correct")}
+    sp = stream.cuda_stream
+
+    def run_per(ft):
+        for pl, o in per[ft]:
+            st = pl.exec_ptr(xs.data_ptr() + 8 * o, ys.data_ptr() + 8 * o, sp)
+            if st != tfl.SUCCESS:
+                raise RuntimeError("per-size exec failed: %d" % st)
+
+    def run_rag(pl):
+        def f():
+            st = pl.exec_ptr(x.data_ptr(), y.data_ptr(), sp)
+            if st != tfl.SUCCESS:
+                raise RuntimeError("ragged exec failed: %d" % st)
+        return f
+
+    reps = max(args.steps, 5)
+    ms = {"ragged_ft": time_calls(run_rag(rag["correct"]), args.warmup, reps, stream),
+          "ragged_plain": time_calls(run_rag(rag["off"]), args.warmup, reps, stream),
+          "ragged_ft_default_shapes": time_calls(run_rag(rag_default), args.warmup, reps, stream),
+          "per_size_plain": time_calls(lambda: run_per("off"), args.warmup, reps, stream),
+          "per_size_ft": time_calls(lambda: run_per("correct"), args.warmup, reps, stream)}
+    rep_ft = rag["correct"].report()
+    # same transforms, same accuracy: ragged ABFT output against the per-size plain output
+    rag["correct"].exec_ptr(x.data_ptr(), y.data_ptr(), sp)
+    run_per("off")
+    torch.cuda.synchronize()
+    diff = float(torch.linalg.vector_norm(y[idx] - ys) / torch.linalg.vector_norm(ys))
+    nbytes = 16.0 * extent
+    members = rag["correct"].members()
+    out = {"workload": "%d complex64 forward transforms, sizes 2^%d..2^%d log-uniform (seed %d), packed, "
+                       "uniform[-1,1) data" % (RAGGED_COUNT, RAGGED_LOG_LO, RAGGED_LOG_HI, RAGGED_SEED),
+           "elements": extent, "bytes_per_exec": nbytes, "reps": reps,
+           "gbs": {k: round(nbytes / (v * 1e-3) / 1e9, 1) for k, v in ms.items()},
+           "ms": {k: round(v, 4) for k, v in ms.items()},
+           "hbm_frac_ragged_ft": round(nbytes / (ms["ragged_ft"] * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+           "abft_overhead_pct": round(100.0 * (ms["ragged_ft"] / ms["ragged_plain"] - 1.0), 2),
+           "vs_per_size_plain": round(ms["per_size_plain"] / ms["ragged_ft"], 4),
+           "autotune_s": round(tune_s, 2),
+           "shapes": [[m["n"], m["batch"], m["radix"][0], m["block"][0], m["per_block"][0]] for m in members],
+           "shapes_columns": ["n", "count", "radix_pass0", "threads_pass0", "per_block_pass0"],
+           "graph_launches_per_exec": 1,
+           "kernel_launches_per_exec": sum(2 * m["num_passes"] for m in members),
+           "rel_l2_vs_per_size_plain": diff,
+           "detected_last_exec": rep_ft["detected"]}
+    for pl in list(rag.values()) + [rag_default] + [q for v in per.values() for q, _ in v]:
+        pl.close()
+    del x, y, xs, ys, idx
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_filter(args, dev, stream):
+    """Differentiable spectral filter y = iFFT(W * FFT(x)), x [64, 128, 4096]
+    complex64, loss = sum |y|^2, forward + backward: through the autograd
+    Functions (ABFT on / off) against the same four transforms issued as
+    plain fixed-size execs with the chain rule written out."""
+    import torch
+
+    import paper_2412_05824_gb300 as tfl
+    from paper_2412_05824_gb300 import autograd as ag
+    import synth_signals as ss
+
+    B, C, N = 64, 128, 4096
+    x0 = ss.uniform_complex_torch(7, B * C, N, "float32", device=dev).view(B, C, N)
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    w0 = torch.complex(torch.randn(C, N, generator=g, device=dev), torch.randn(C, N, generator=g, device=dev))
+    w0 = w0 * (N ** -0.5 / 2 ** 0.5)
+
+    def autograd_step(ft):
+        def f():
+            x = x0.detach().requires_grad_(True)
+            w = w0.detach().requires_grad_(True)
+            loss = ag.spectral_filter(x, w, ft).abs().pow(2).sum()
+            loss.backward()
+            return x.grad, w.grad
+        return f
+
+    plans = {d: tfl.Plan(N, B * C, "complex64", d, "off") for d in ("forward", "inverse", "forward_scaled",
+                                                                   "inverse_unscaled")}
+
+    def plain_step():
+        X = plans["forward"].exec(x0.view(B * C, N)).view(B, C, N)
+        Z = X * w0
+        Y = plans["inverse"].exec(Z.view(B * C, N)).view(B, C, N)
+        gY = 2.0 * Y
+        gZ = plans["forward_scaled"].exec(gY.view(B * C, N)).view(B, C, N)
+        gw = (X.conj() * gZ).sum(0)
+        gX = w0.conj() * gZ
+        gx = plans["inverse_unscaled"].exec(gX.view(B * C, N)).view(B, C, N)
+        return gx, gw
+
+    def torch_step():
+        x = x0.detach().requires_grad_(True)
+        w = w0.detach().requires_grad_(True)
+        loss = torch.fft.ifft(torch.fft.fft(x) * w).abs().pow(2).sum()
+        loss.backward()
+        return x.grad, w.grad
+
+    reps = max(args.steps, 5)
+    ms = {"autograd_ft": time_calls(autograd_step("correct"), args.warmup, reps, stream),
+          "autograd_plain": time_calls(autograd_step("off"), args.warmup, reps, stream),
+          "plain_fixed_size": time_calls(plain_step, args.warmup, reps, stream),
+          "torch_fft_context": time_calls(torch_step, args.warmup, reps, stream)}
+    gx_a, gw_a = autograd_step("correct")()
+    gx_p, gw_p = plain_step()
+    gx_t, gw_t = torch_step()
+
+    def rel(a, b):
+        return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+    out = {"workload": "x [64,128,4096] complex64 uniform[-1,1), W [128,4096] complex normal (std 1/64), "
+                       "loss = sum|iFFT(W*FFT(x))|^2, forward + backward",
+           "ms": {k: round(v, 4) for k, v in ms.items()},
+           "autograd_overhead_vs_plain_pct": round(100.0 * (ms["autograd_plain"] / ms["plain_fixed_size"] - 1.0), 2),
+           "abft_overhead_pct": round(100.0 * (ms["autograd_ft"] / ms["autograd_plain"] - 1.0), 2),
+           "transforms_per_step": 4,
+           "rel_l2_grad_x_autograd_vs_plain": rel(gx_a, gx_p),
+           "rel_l2_grad_w_autograd_vs_plain": rel(gw_a, gw_p),
+           "rel_l2_grad_x_vs_torch_fft": rel(gx_a, gx_t),
+           "note": "torch_fft_context is the same step through torch.fft, for context only"}
+    for pl in plans.values():
+        pl.close()
+    ag._plans.clear()
+    return out
+
+
+# ---------------------------------------------------------------------------
 # our implementation
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -388,6 +576,9 @@ def run_ours(args):
                "sample": "oracle (float64 radix-2, OpenMP) on 2^19 elements per sweep configuration "
                          "(%.1f s of CPU work); GB/s by the same byte formula" % s}
 
+    ragged = bench_ragged(args, dev, stream, rank, peaks) if not args.no_ragged else None
+    sfilter = bench_filter(args, dev, stream) if not args.no_filter else None
+
     launches_per_step = 0
     for dt2, eb2, d2, n2 in cfgs:
         launches_per_step += plans_ft[(dt2, d2, n2)].info()["num_passes"] * 2
@@ -421,7 +612,9 @@ def run_ours(args):
                 "false_alarms_last_step": fa,
                 "per_dtype": per_dtype,
                 "sweep_columns": ["dtype", "dir", "log2N", "ft_GBs", "plain_GBs", "ft_GFLOPs"],
-                "sweep": sweep}
+                "sweep": sweep,
+                "ragged": ragged,
+                "spectral_filter": sfilter}
         print(json.dumps(line), flush=True)
     for pl in list(plans_ft.values()) + list(plans_plain.values()):
         pl.close()

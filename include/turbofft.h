@@ -136,6 +136,9 @@ typedef struct {
   int32_t block[2];         /* threads per block per pass */
   int64_t workspace_bytes;  /* device memory the plan owns or will allocate */
   int64_t scratch_bytes;    /* intermediate buffer of a two-pass plan (0 for one pass) */
+  int32_t per_block[2];     /* transforms (SP) / columns / rows one block holds per transaction */
+  int32_t num_members;      /* ragged plan: distinct sizes (member plans); 0 otherwise */
+  int32_t autotuned;        /* 1 if launch shapes were chosen by timing (turbofft_set_autotune) */
 } turbofft_plan_info;
 
 /* Duration of one kernel of the last exec (turbofft_set_profiling). */
@@ -162,6 +165,59 @@ typedef struct {
 turbofft_status turbofft_plan_create(int64_t n, int64_t batch, turbofft_dtype dtype,
                                      int direction, turbofft_ft_mode ft_mode,
                                      turbofft_plan **plan);
+
+/*
+ * Ragged batch: `count` transforms of mixed power-of-two lengths in one plan
+ * (a batching facility; the paper's kernels take one length per launch).
+ *   sizes[i]    length of transform i, a power of two in [8, 2^24]
+ *   offsets[i]  element offset of transform i in the packed buffers given
+ *               to turbofft_exec; F32 offsets must be even (each transform
+ *               starts on a 16-byte boundary); transforms may not overlap,
+ *               gaps are allowed and never touched
+ *   count       >= 1
+ *   dtype, direction, ft_mode: as turbofft_plan_create; one group of
+ *               equal-length transforms per distinct size may hold at most
+ *               2^31 elements
+ * The plan holds one member plan per distinct size (turbofft_plan_get_member_info,
+ * members in ascending size order) whose kernels address their transforms
+ * through a device copy of the offsets.  turbofft_exec on a ragged plan
+ * launches ONE CUDA graph on `stream` in which the members' kernels are
+ * parallel branches; the graph is captured on the first exec and captured
+ * again whenever `in` or `out` differ from the last captured pair (a
+ * synchronous step: do not exec a ragged plan with new pointers inside a
+ * stream capture of your own).  An exec with a site armed by
+ * turbofft_inject queues the members' kernels directly instead.  The packed
+ * buffers span max(offsets[i] + sizes[i]) elements.  turbofft_get_report
+ * sums the members' reports, transform indices are the global ones (i), and
+ * turbofft_inject takes the global transform index.  turbofft_exec_host
+ * copies the whole packed span in, runs the graph and copies it out.
+ * turbofft_set_workspace, turbofft_set_profiling and
+ * turbofft_exec_static_scratch return TURBOFFT_UNSUPPORTED on ragged plans.
+ * With autotuning on, every member is tuned on its own indexed geometry.
+ * Errors: INVALID_VALUE (NULL arrays, count < 1, a bad size, a negative,
+ * odd (F32) or overlapping offset), ALLOC_FAILED, CUDA_ERROR.
+ */
+turbofft_status turbofft_plan_create_ragged(const int64_t *sizes, const int64_t *offsets, int64_t count,
+                                            turbofft_dtype dtype, int direction,
+                                            turbofft_ft_mode ft_mode, turbofft_plan **plan);
+
+/* Facts about member `index` (ascending size order) of a ragged plan;
+ * INVALID_VALUE for a plan that is not ragged or an index out of range. */
+turbofft_status turbofft_plan_get_member_info(const turbofft_plan *plan, int32_t index,
+                                              turbofft_plan_info *info);
+
+/*
+ * Autotuning of launch shapes (process-wide switch, off by default).  When
+ * on, every plan created afterwards times each registered shape of each of
+ * its passes -- radix (complex values per thread), threads per transform
+ * and transforms per thread block -- on its own geometry (its batch, length,
+ * fault-tolerance mode and, for ragged members, offsets) and keeps the
+ * fastest.  The timing runs at plan creation on temporary buffers the size
+ * of the plan's data (no tuning if they cannot be allocated) and is cached
+ * per process.  Results do not depend on the shape: every shape computes
+ * the same transform.  Returns SUCCESS.
+ */
+turbofft_status turbofft_set_autotune(int enable);
 
 /*
  * Transform `in` into `out` (both device pointers, see the layout above) on

@@ -67,7 +67,8 @@ class PlanInfo(ctypes.Structure):
                 ("stages", ctypes.c_int32 * 2), ("radix", ctypes.c_int32 * 2),
                 ("group_transactions", ctypes.c_int32), ("grid", ctypes.c_int32 * 2),
                 ("block", ctypes.c_int32 * 2), ("workspace_bytes", ctypes.c_int64),
-                ("scratch_bytes", ctypes.c_int64)]
+                ("scratch_bytes", ctypes.c_int64), ("per_block", ctypes.c_int32 * 2),
+                ("num_members", ctypes.c_int32), ("autotuned", ctypes.c_int32)]
 
 
 class KernelTime(ctypes.Structure):
@@ -79,7 +80,8 @@ EXPORTS = [
     "turbofft_get_report", "turbofft_plan_get_info", "turbofft_set_threshold_scale",
     "turbofft_destroy", "turbofft_status_string", "turbofft_last_error",
     "turbofft_set_workspace", "turbofft_set_profiling", "turbofft_get_kernel_times",
-    "turbofft_exec_static_scratch",
+    "turbofft_exec_static_scratch", "turbofft_plan_create_ragged", "turbofft_plan_get_member_info",
+    "turbofft_set_autotune",
 ]
 
 STATIC_SCRATCH_BYTES = 32 << 20
@@ -100,6 +102,10 @@ def lib() -> ctypes.CDLL:
     L.turbofft_exec.argtypes = [vp, vp, vp, vp]
     L.turbofft_exec_host.argtypes = [vp, vp, vp, vp]
     L.turbofft_exec_static_scratch.argtypes = [vp, vp, vp, vp]
+    L.turbofft_plan_create_ragged.argtypes = [ctypes.POINTER(i64), ctypes.POINTER(i64), i64, i32, i32, i32,
+                                              ctypes.POINTER(vp)]
+    L.turbofft_plan_get_member_info.argtypes = [vp, i32, ctypes.POINTER(PlanInfo)]
+    L.turbofft_set_autotune.argtypes = [i32]
     L.turbofft_inject.argtypes = [vp, Site, i32]
     L.turbofft_get_report.argtypes = [vp, ctypes.POINTER(Report)]
     L.turbofft_plan_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
@@ -182,10 +188,13 @@ class Plan:
     def exec_host(self, x_host, out_host=None, stream=None):
         """Transform CPU (ideally pinned) tensors: copies in, transforms, copies out."""
         import torch
-        if x_host.is_cuda or x_host.dtype != self.torch_dtype or not x_host.is_contiguous():
-            raise ValueError("x_host must be a contiguous CPU %s tensor" % self.torch_dtype)
+        span = self.extent if isinstance(self, RaggedPlan) else self.n * self.batch
+        if x_host.is_cuda or x_host.dtype != self.torch_dtype or not x_host.is_contiguous() or x_host.numel() < span:
+            raise ValueError("x_host must be a contiguous CPU %s tensor of >= %d elements" % (self.torch_dtype, span))
         if out_host is None:
             out_host = torch.empty_like(x_host)
+        if out_host.is_cuda or out_host.dtype != self.torch_dtype or not out_host.is_contiguous() or out_host.numel() < span:
+            raise ValueError("out_host must be a contiguous CPU %s tensor of >= %d elements" % (self.torch_dtype, span))
         s = 0 if stream is None else stream.cuda_stream
         _check(lib().turbofft_exec_host(self._h, x_host.data_ptr(), out_host.data_ptr(), s), "turbofft_exec_host", self._h)
         return out_host
@@ -206,11 +215,7 @@ class Plan:
     def info(self) -> dict:
         i = PlanInfo()
         _check(lib().turbofft_plan_get_info(self._h, ctypes.byref(i)), "turbofft_plan_get_info")
-        d = {}
-        for name, _ in PlanInfo._fields_:
-            v = getattr(i, name)
-            d[name] = list(v) if hasattr(v, "__len__") else v
-        return d
+        return _info_dict(i)
 
     def set_workspace(self, buf):
         """Use the CUDA tensor `buf` (kept alive by the plan object) as the
@@ -242,6 +247,75 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def _info_dict(i: PlanInfo) -> dict:
+    d = {}
+    for name, _ in PlanInfo._fields_:
+        v = getattr(i, name)
+        d[name] = list(v) if hasattr(v, "__len__") else v
+    return d
+
+
+def set_autotune(enable: bool = True):
+    """Process-wide: plans created afterwards time their candidate launch
+    shapes and keep the fastest (turbofft_set_autotune)."""
+    _check(lib().turbofft_set_autotune(1 if enable else 0), "turbofft_set_autotune")
+
+
+def packed_offsets(sizes, dtype="complex64"):
+    """Offsets of transforms of the given sizes packed back to back in order
+    (every size is a power of two >= 8, so each start stays 16-byte aligned);
+    returns (offsets, total elements)."""
+    offs, o = [], 0
+    for n in sizes:
+        offs.append(o)
+        o += int(n)
+    return offs, o
+
+
+class RaggedPlan(Plan):
+    """Transforms of mixed power-of-two sizes at given element offsets of one
+    packed buffer, run as one CUDA graph (turbofft_plan_create_ragged)."""
+
+    def __init__(self, sizes, offsets, dtype="complex64", direction="forward", ft="off"):
+        sizes = [int(v) for v in sizes]
+        offsets = [int(v) for v in offsets]
+        if len(sizes) != len(offsets):
+            raise ValueError("sizes and offsets differ in length")
+        self.sizes, self.offsets = sizes, offsets
+        self.n, self.batch = 0, len(sizes)
+        self.extent = max((o + n for o, n in zip(offsets, sizes)), default=0)
+        self.dtype_code = _dtype_code(dtype)
+        self.direction = _DIRS[direction]
+        self.ft_mode = _FT[ft]
+        arr = ctypes.c_int64 * max(1, len(sizes))
+        h = ctypes.c_void_p()
+        _check(lib().turbofft_plan_create_ragged(arr(*sizes), arr(*offsets), len(sizes), self.dtype_code,
+                                                 self.direction, self.ft_mode, ctypes.byref(h)),
+               "turbofft_plan_create_ragged")
+        self._h = h
+
+    def exec(self, x, out=None, stream=None):
+        """Transform the packed CUDA tensor x (1-D, at least `extent` elements)."""
+        import torch
+        if not (x.is_cuda and x.dtype == self.torch_dtype and x.is_contiguous() and x.numel() >= self.extent):
+            raise ValueError("x must be a contiguous CUDA %s tensor with >= %d elements" % (self.torch_dtype, self.extent))
+        if out is None:
+            out = torch.empty_like(x)
+        if stream is None:
+            stream = torch.cuda.current_stream(x.device)
+        _check(lib().turbofft_exec(self._h, x.data_ptr(), out.data_ptr(), stream.cuda_stream), "turbofft_exec", self._h)
+        return out
+
+    def member_info(self, index: int) -> dict:
+        i = PlanInfo()
+        _check(lib().turbofft_plan_get_member_info(self._h, int(index), ctypes.byref(i)),
+               "turbofft_plan_get_member_info")
+        return _info_dict(i)
+
+    def members(self) -> list:
+        return [self.member_info(k) for k in range(self.info()["num_members"])]
 
 
 _plan_cache: dict = {}

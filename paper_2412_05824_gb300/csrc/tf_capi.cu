@@ -13,8 +13,12 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <complex>
+#include <map>
 #include <mutex>
+#include <numeric>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -36,17 +40,26 @@ struct Registry {
   std::vector<const KernelEntry*> all;
   Registry() {
     tf::EntryTableFn fns[] = {tf::entries_f32_sp, tf::entries_f32_col, tf::entries_f32_row,
-                              tf::entries_f64_sp, tf::entries_f64_col, tf::entries_f64_row};
+                              tf::entries_f64_sp, tf::entries_f64_col, tf::entries_f64_row,
+                              tf::entries_f32_alt_sp, tf::entries_f32_alt_cr};
     for (auto fn : fns) {
       int n = 0;
       const KernelEntry* t = fn(&n);
       for (int i = 0; i < n; ++i) all.push_back(&t[i]);
     }
   }
+  // the first registered entry is the default shape; later ones are
+  // alternatives the autotuner may pick
   const KernelEntry* find(int dtype, int kind, int ns) const {
     for (auto e : all)
       if (e->dtype == dtype && e->kind == kind && e->ns == ns) return e;
     return nullptr;
+  }
+  std::vector<const KernelEntry*> find_all(int dtype, int kind, int ns) const {
+    std::vector<const KernelEntry*> v;
+    for (auto e : all)
+      if (e->dtype == dtype && e->kind == kind && e->ns == ns) v.push_back(e);
+    return v;
   }
   int max_sp(int dtype) const {
     int m = 0;
@@ -185,6 +198,24 @@ struct turbofft_plan {
   int nprof = 0;
   cudaEvent_t prof_ev[8][2] = {};
   int prof_kind[8] = {};
+  // member of a ragged plan: element offsets of its transforms in the
+  // caller's packed buffers (device), null for the contiguous layout
+  long long* d_tab = nullptr;
+  // ragged plan: one member plan per distinct size, run as the parallel
+  // branches of one CUDA graph
+  bool ragged = false;
+  std::vector<turbofft_plan*> members;
+  std::vector<std::vector<int64_t>> member_ids;  // global transform index of each member transform
+  int64_t extent = 0;                             // elements spanned by the packed buffers
+  std::vector<cudaStream_t> branch_streams;
+  std::vector<cudaEvent_t> branch_events;
+  cudaGraphExec_t graph_exec = nullptr;
+  const void* graph_in = nullptr;
+  void* graph_out = nullptr;
+  bool armed_any = false;
+  std::vector<int32_t> member_of;  // ragged: member plan of each global transform
+  std::vector<int64_t> local_of;   // ragged: index of each global transform within its member
+  bool autotuned = false;          // launch shapes chosen by timing (turbofft_set_autotune)
 };
 
 namespace {
@@ -290,6 +321,8 @@ void fill_args(const turbofft_plan* p, int pi, const void* in, void* out, int64_
   A.geo.n1 = p->n1;
   A.geo.n2 = p->n2;
   A.geo.batch = batch;
+  A.geo.in_tab = (pi == 0) ? p->d_tab : nullptr;
+  A.geo.out_tab = (pi == p->num_passes - 1) ? p->d_tab : nullptr;
   A.num_units = units_for(p, pi, batch);
   const bool inverse = p->direction > 0;
   const bool scaled = p->direction == TURBOFFT_INVERSE || p->direction == TURBOFFT_FORWARD_SCALED;
@@ -386,6 +419,270 @@ cudaError_t stage_reserve(HostStage& hs, size_t need) {
   return cudaSuccess;
 }
 
+// queue one complete exec of a (member) plan on `s`: report reset, kernels,
+// report copy to the pinned host mirror
+turbofft_status queue_plan(turbofft_plan* p, const void* in, void* out, void* scratch, cudaStream_t s,
+                           const tf::InjectSite& inj) {
+  const bool ft = p->ft_mode != TURBOFFT_FT_OFF;
+  if (ft) {
+    cudaError_t e = cudaMemsetAsync(p->d_fts, 0, tf::FT_HEADER_BYTES, s);
+    if (e != cudaSuccess) return cuda_fail(p, e, "report reset");
+  }
+  turbofft_status st = run(p, in, out, scratch, p->batch, 0, s, inj);
+  if (st != TURBOFFT_SUCCESS) return st;
+  if (ft) {
+    cudaError_t e = cudaMemcpyAsync(p->h_fts, p->d_fts, sizeof(FtState), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(p, e, "report copy");
+  }
+  return TURBOFFT_SUCCESS;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: every registered shape of a pass (radix = values per thread,
+// threads per transform, transforms per block) is timed on the plan's own
+// geometry and the fastest kept.  Results are cached per process.
+// ---------------------------------------------------------------------------
+std::atomic<int> g_autotune{0};
+thread_local bool t_defer_tune = false;  // ragged members are tuned after their offsets are set
+std::mutex g_tune_mu;
+typedef std::tuple<int, int, int64_t, int64_t, int, int> TuneKey;  // dtype, pass, n, batch, variant, indexed
+std::map<TuneKey, const KernelEntry*> g_tune_cache;
+
+bool use_entry(turbofft_plan* p, int pi, const KernelEntry* ke) {
+  if (!set_smem_attrs(ke)) {
+    cudaGetLastError();
+    return false;
+  }
+  p->pass[pi].ke = ke;
+  p->pass[pi].grid = occupancy_blocks(ke, ft_variant(p->ft_mode)) * g_num_sms;
+  return true;
+}
+
+// time each candidate of each pass on (in, out, scratch), which span the
+// plan's buffers; keeps the default shape of a pass whose candidates all fail
+void autotune(turbofft_plan* p, const void* in, void* out, void* scratch) {
+  const Registry& reg = registry();
+  const int dt = p->dtype == TURBOFFT_C2C_F32 ? 0 : 1;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    if (s) cudaStreamDestroy(s);
+    if (e0) cudaEventDestroy(e0);
+    return;
+  }
+  const tf::InjectSite none{};
+  for (int pi = 0; pi < p->num_passes; ++pi) {
+    const PassPlan& pp = p->pass[pi];
+    std::vector<const KernelEntry*> cands = reg.find_all(dt, pp.kind, pp.ns);
+    if (cands.size() < 2) continue;
+    const TuneKey key(dt, pi, p->n, p->batch, ft_variant(p->ft_mode), p->d_tab ? 1 : 0);
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) {
+        use_entry(p, pi, it->second);
+        continue;
+      }
+    }
+    const KernelEntry* dflt = pp.ke;
+    const KernelEntry* best = nullptr;
+    float best_ms = 0.f;
+    for (const KernelEntry* ke : cands) {
+      if (!use_entry(p, pi, ke)) continue;
+      bool ok = queue_plan(p, in, out, scratch, s, none) == TURBOFFT_SUCCESS;  // warm-up
+      float ms_min = 0.f;
+      for (int rep = 0; ok && rep < 3; ++rep) {
+        ok = cudaEventRecord(e0, s) == cudaSuccess && queue_plan(p, in, out, scratch, s, none) == TURBOFFT_SUCCESS &&
+             cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+        float ms = 0.f;
+        if (ok) ok = cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+        if (ok && (rep == 0 || ms < ms_min)) ms_min = ms;
+      }
+      if (!ok) {
+        cudaStreamSynchronize(s);
+        cudaGetLastError();
+        continue;
+      }
+      if (!best || ms_min < best_ms) {
+        best = ke;
+        best_ms = ms_min;
+      }
+    }
+    if (!best) best = dflt;
+    use_entry(p, pi, best);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = best;
+  }
+  cudaStreamSynchronize(s);
+  if (p->d_fts) cudaMemset(p->d_fts, 0, sizeof(FtState));
+  if (p->h_fts) memset(p->h_fts, 0, sizeof(FtState));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  cudaGetLastError();
+  p->autotuned = true;
+}
+
+// autotune a contiguous plan on temporary buffers of its own size (nothing
+// is tuned if they cannot be allocated)
+void autotune_with_temp(turbofft_plan* p) {
+  const size_t bytes = (size_t)(p->batch * p->n) * elem_bytes(p->dtype);
+  void *a = nullptr, *b = nullptr, *c = nullptr;
+  bool ok = cudaMalloc(&a, bytes) == cudaSuccess && cudaMalloc(&b, bytes) == cudaSuccess &&
+            (p->num_passes == 1 || cudaMalloc(&c, p->scratch_bytes) == cudaSuccess);
+  // a finite, non-zero pattern (0x3c bytes) so that timing sees ordinary arithmetic
+  if (ok) ok = cudaMemset(a, 0x3c, bytes) == cudaSuccess;
+  if (ok) autotune(p, a, b, c);
+  cudaGetLastError();
+  for (void* q : {a, b, c})
+    if (q) cudaFree(q);
+}
+
+// ---------------------------------------------------------------------------
+// ragged plans
+// ---------------------------------------------------------------------------
+void drop_graph(turbofft_plan* p) {
+  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+  p->graph_exec = nullptr;
+  p->graph_in = nullptr;
+  p->graph_out = nullptr;
+}
+
+// capture the members as parallel branches of one graph reading `in` and
+// writing `out`
+turbofft_status capture_ragged(turbofft_plan* p, const void* in, void* out) {
+  drop_graph(p);
+  cudaStream_t cs = p->branch_streams[0];
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(p, e, "graph capture");
+  turbofft_status st = TURBOFFT_SUCCESS;
+  const tf::InjectSite none{};
+  e = cudaEventRecord(p->branch_events[0], cs);
+  for (size_t k = 0; e == cudaSuccess && st == TURBOFFT_SUCCESS && k < p->members.size(); ++k) {
+    turbofft_plan* m = p->members[k];
+    cudaStream_t bs = p->branch_streams[k + 1];
+    e = cudaStreamWaitEvent(bs, p->branch_events[0], 0);
+    if (e != cudaSuccess) break;
+    st = queue_plan(m, in, out, m->d_scratch, bs, none);
+    if (st != TURBOFFT_SUCCESS) break;
+    e = cudaEventRecord(p->branch_events[k + 1], bs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, p->branch_events[k + 1], 0);
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess && st == TURBOFFT_SUCCESS) e = cudaGraphInstantiate(&p->graph_exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (st != TURBOFFT_SUCCESS || e != cudaSuccess) {
+    p->graph_exec = nullptr;
+    cudaGetLastError();
+    if (st != TURBOFFT_SUCCESS) {
+      for (auto m : p->members)
+        if (!m->last_error.empty()) p->last_error = m->last_error;
+      return st;
+    }
+    return cuda_fail(p, e, "graph capture");
+  }
+  p->graph_in = in;
+  p->graph_out = out;
+  return TURBOFFT_SUCCESS;
+}
+
+turbofft_status exec_ragged(turbofft_plan* p, const void* in, void* out, cudaStream_t s) {
+  for (auto m : p->members)
+    if (m->num_passes == 2 && !m->d_scratch) {
+      if (!dev_alloc(m, &m->d_scratch, m->scratch_bytes)) return TURBOFFT_ALLOC_FAILED;
+      m->scratch_owned = true;
+    }
+  if (p->armed_any) {
+    // an armed site: queue the members directly (the graph holds no site)
+    p->armed_any = false;
+    for (auto m : p->members) {
+      tf::InjectSite inj = m->armed;
+      m->armed.active = 0;
+      turbofft_status st = queue_plan(m, in, out, m->d_scratch, s, inj);
+      if (st != TURBOFFT_SUCCESS) {
+        p->last_error = m->last_error;
+        return st;
+      }
+    }
+  } else {
+    if (!p->graph_exec || p->graph_in != in || p->graph_out != out) {
+      turbofft_status st = capture_ragged(p, in, out);
+      if (st != TURBOFFT_SUCCESS) return st;
+    }
+    cudaError_t e = cudaGraphLaunch(p->graph_exec, s);
+    if (e != cudaSuccess) return cuda_fail(p, e, "graph launch");
+  }
+  cudaError_t e = cudaEventRecord(p->done, s);
+  if (e != cudaSuccess) return cuda_fail(p, e, "event record");
+  p->have_exec = true;
+  return TURBOFFT_SUCCESS;
+}
+
+// add a (member) plan's last report into *r; `ids` maps its transforms to
+// global indices (ragged members)
+void add_report(const turbofft_plan* m, const std::vector<int64_t>* ids, turbofft_report* r) {
+  const FtState& h = *m->h_fts;
+  r->groups_checked += (int64_t)h.groups;
+  r->detected += (int64_t)h.detected;
+  r->located += (int64_t)h.located;
+  r->corrected += (int64_t)h.corrected;
+  r->recomputed += (int64_t)h.recomputed;
+  r->uncorrectable += (int64_t)(h.uncorrectable + h.dropped);
+  r->max_clean_ratio = std::max(r->max_clean_ratio, (double)h.max_clean_ratio);
+  const int nrec = (int)std::min<unsigned long long>(h.num_records, tf::MAX_RECORDS);
+  for (int i = 0; i < nrec; ++i) {
+    const FtRecord& rc = h.rec[i];
+    if (r->first_pass < 0) {
+      r->first_pass = rc.pass_id;
+      r->first_residual = sqrt(rc.s1r * rc.s1r + rc.s1i * rc.s1i);
+      r->first_threshold = rc.tau;
+    }
+    if (rc.signal >= 0 && r->first_transform < 0) {
+      const int kind = m->pass[rc.pass_id].kind;
+      int64_t tr = rc.signal;
+      if (kind == tf::KIND_COL) tr = rc.signal / m->n2;
+      if (kind == tf::KIND_ROW) tr = rc.signal / m->n1;
+      tr += rc.transform_base;
+      r->first_transform = (ids && tr >= 0 && tr < (int64_t)ids->size()) ? (*ids)[tr] : tr;
+    }
+  }
+}
+
+void fill_info(const turbofft_plan* p, turbofft_plan_info* info) {
+  memset(info, 0, sizeof(*info));
+  info->n = p->n;
+  info->batch = p->batch;
+  info->dtype = p->dtype;
+  info->direction = p->direction;
+  info->ft_mode = p->ft_mode;
+  info->autotuned = p->autotuned ? 1 : 0;
+  info->group_transactions = p->T;
+  if (p->ragged) {
+    info->num_members = (int32_t)p->members.size();
+    for (auto m : p->members) {
+      info->workspace_bytes += m->workspace_bytes + (m->scratch_owned ? 0 : (int64_t)m->scratch_bytes);
+      info->autotuned |= m->autotuned ? 1 : 0;
+    }
+    return;
+  }
+  info->num_passes = p->num_passes;
+  for (int pi = 0; pi < p->num_passes; ++pi) {
+    info->sub_n[pi] = p->pass[pi].ns;
+    info->stages[pi] = p->pass[pi].ke->stages;
+    info->radix[pi] = p->pass[pi].ke->e;
+    info->grid[pi] = p->pass[pi].grid;
+    info->block[pi] = p->pass[pi].ke->nt;
+    info->per_block[pi] = p->pass[pi].ke->s;
+  }
+  if (p->num_passes == 1) info->sub_n[1] = 1;
+  info->workspace_bytes = p->workspace_bytes + (p->scratch_owned ? 0 : (int64_t)p->scratch_bytes);
+  info->scratch_bytes = (int64_t)p->scratch_bytes;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -414,6 +711,12 @@ turbofft_status turbofft_destroy(turbofft_plan* p) {
   cudaGetDevice(&cur);
   cudaSetDevice(p->device);
   cudaDeviceSynchronize();
+  for (auto m : p->members) turbofft_destroy(m);
+  drop_graph(p);
+  for (auto st : p->branch_streams)
+    if (st) cudaStreamDestroy(st);
+  for (auto ev : p->branch_events)
+    if (ev) cudaEventDestroy(ev);
   for (void* a : p->allocs) cudaFree(a);
   if (p->h_fts) cudaFreeHost(p->h_fts);
   if (p->done) cudaEventDestroy(p->done);
@@ -535,41 +838,156 @@ turbofft_status turbofft_plan_create(int64_t n, int64_t batch, turbofft_dtype dt
     turbofft_destroy(p);
     return TURBOFFT_CUDA_ERROR;
   }
+  if (g_autotune.load() && !t_defer_tune) autotune_with_temp(p);
   *out = p;
+  return TURBOFFT_SUCCESS;
+}
+
+turbofft_status turbofft_plan_create_ragged(const int64_t* sizes, const int64_t* offsets, int64_t count,
+                                            turbofft_dtype dtype, int direction, turbofft_ft_mode ft_mode,
+                                            turbofft_plan** out) {
+  if (!out) return TURBOFFT_INVALID_VALUE;
+  *out = nullptr;
+  if (!sizes || !offsets || count < 1 || count > ((int64_t)1 << 31)) return TURBOFFT_INVALID_VALUE;
+  if (dtype != TURBOFFT_C2C_F32 && dtype != TURBOFFT_C2C_F64) return TURBOFFT_INVALID_VALUE;
+  if (direction != TURBOFFT_FORWARD && direction != TURBOFFT_INVERSE && direction != TURBOFFT_INVERSE_UNSCALED &&
+      direction != TURBOFFT_FORWARD_SCALED)
+    return TURBOFFT_INVALID_VALUE;
+  if (ft_mode != TURBOFFT_FT_OFF && ft_mode != TURBOFFT_FT_DETECT && ft_mode != TURBOFFT_FT_CORRECT &&
+      ft_mode != TURBOFFT_FT_CORRECT_REGISTERS)
+    return TURBOFFT_INVALID_VALUE;
+  int64_t extent = 0;
+  for (int64_t i = 0; i < count; ++i) {
+    const int lg = ilog2_exact(sizes[i]);
+    if (lg < 3 || lg > 24 || offsets[i] < 0 || offsets[i] > ((int64_t)1 << 40)) return TURBOFFT_INVALID_VALUE;
+    // every transform starts on a 16-byte boundary of the packed buffers
+    if (dtype == TURBOFFT_C2C_F32 && (offsets[i] & 1)) return TURBOFFT_INVALID_VALUE;
+    extent = std::max(extent, offsets[i] + sizes[i]);
+  }
+  std::vector<int64_t> order((size_t)count);
+  std::iota(order.begin(), order.end(), (int64_t)0);
+  std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return offsets[a] < offsets[b]; });
+  for (size_t k = 1; k < order.size(); ++k)
+    if (offsets[order[k - 1]] + sizes[order[k - 1]] > offsets[order[k]]) return TURBOFFT_INVALID_VALUE;
+
+  std::map<int64_t, std::vector<int64_t>> groups;  // size -> global indices, ascending
+  for (int64_t i = 0; i < count; ++i) groups[sizes[i]].push_back(i);
+  for (auto& g : groups)
+    if ((int64_t)g.second.size() * g.first > ((int64_t)1 << 31)) return TURBOFFT_INVALID_VALUE;
+
+  turbofft_plan* p = new turbofft_plan();
+  p->ragged = true;
+  p->n = 0;
+  p->batch = count;
+  p->dtype = dtype;
+  p->direction = direction;
+  p->ft_mode = ft_mode;
+  p->extent = extent;
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return TURBOFFT_CUDA_ERROR;
+  }
+  p->member_of.assign((size_t)count, 0);
+  p->local_of.assign((size_t)count, 0);
+  t_defer_tune = true;
+  turbofft_status st = TURBOFFT_SUCCESS;
+  for (auto& g : groups) {
+    turbofft_plan* m = nullptr;
+    st = turbofft_plan_create(g.first, (int64_t)g.second.size(), dtype, direction, ft_mode, &m);
+    if (st != TURBOFFT_SUCCESS) break;
+    p->members.push_back(m);
+    p->member_ids.push_back(g.second);
+    std::vector<long long> tab(g.second.size());
+    for (size_t j = 0; j < tab.size(); ++j) {
+      tab[j] = offsets[g.second[j]];
+      p->member_of[(size_t)g.second[j]] = (int32_t)(p->members.size() - 1);
+      p->local_of[(size_t)g.second[j]] = (int64_t)j;
+    }
+    void* d = nullptr;
+    if (!dev_alloc(m, &d, tab.size() * sizeof(long long)) ||
+        cudaMemcpy(d, tab.data(), tab.size() * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      st = TURBOFFT_ALLOC_FAILED;
+      break;
+    }
+    m->d_tab = static_cast<long long*>(d);
+  }
+  t_defer_tune = false;
+  if (st != TURBOFFT_SUCCESS) {
+    turbofft_destroy(p);
+    return st;
+  }
+  const size_t nstreams = p->members.size() + 1;
+  p->branch_streams.assign(nstreams, nullptr);
+  p->branch_events.assign(nstreams, nullptr);
+  for (size_t k = 0; k < nstreams; ++k)
+    if (cudaStreamCreateWithFlags(&p->branch_streams[k], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->branch_events[k], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      turbofft_destroy(p);
+      return TURBOFFT_CUDA_ERROR;
+    }
+  if (cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    turbofft_destroy(p);
+    return TURBOFFT_CUDA_ERROR;
+  }
+  if (g_autotune.load()) {
+    // tune every member on its real (indexed) geometry in shared temporaries
+    const size_t bytes = (size_t)extent * elem_bytes(dtype);
+    size_t sbytes = 0;
+    for (auto m : p->members) sbytes = std::max(sbytes, m->num_passes == 2 ? m->scratch_bytes : (size_t)0);
+    void *a = nullptr, *b = nullptr, *c = nullptr;
+    bool ok = cudaMalloc(&a, bytes) == cudaSuccess && cudaMalloc(&b, bytes) == cudaSuccess &&
+              (sbytes == 0 || cudaMalloc(&c, sbytes) == cudaSuccess);
+    if (ok) ok = cudaMemset(a, 0x3c, bytes) == cudaSuccess;
+    if (ok)
+      for (auto m : p->members) autotune(m, a, b, c);
+    cudaGetLastError();
+    for (void* q : {a, b, c})
+      if (q) cudaFree(q);
+  }
+  *out = p;
+  return TURBOFFT_SUCCESS;
+}
+
+turbofft_status turbofft_plan_get_member_info(const turbofft_plan* p, int32_t index, turbofft_plan_info* info) {
+  if (!p || !info || !p->ragged || index < 0 || index >= (int32_t)p->members.size()) return TURBOFFT_INVALID_VALUE;
+  fill_info(p->members[(size_t)index], info);
+  return TURBOFFT_SUCCESS;
+}
+
+turbofft_status turbofft_set_autotune(int enable) {
+  g_autotune.store(enable ? 1 : 0);
   return TURBOFFT_SUCCESS;
 }
 
 turbofft_status turbofft_plan_get_info(const turbofft_plan* p, turbofft_plan_info* info) {
   if (!p || !info) return TURBOFFT_INVALID_VALUE;
-  memset(info, 0, sizeof(*info));
-  info->n = p->n;
-  info->batch = p->batch;
-  info->dtype = p->dtype;
-  info->direction = p->direction;
-  info->ft_mode = p->ft_mode;
-  info->num_passes = p->num_passes;
-  for (int pi = 0; pi < p->num_passes; ++pi) {
-    info->sub_n[pi] = p->pass[pi].ns;
-    info->stages[pi] = p->pass[pi].ke->stages;
-    info->radix[pi] = p->pass[pi].ke->e;
-    info->grid[pi] = p->pass[pi].grid;
-    info->block[pi] = p->pass[pi].ke->nt;
-  }
-  if (p->num_passes == 1) info->sub_n[1] = 1;
-  info->group_transactions = p->T;
-  info->workspace_bytes = p->workspace_bytes + (p->scratch_owned ? 0 : (int64_t)p->scratch_bytes);
-  info->scratch_bytes = (int64_t)p->scratch_bytes;
+  fill_info(p, info);
   return TURBOFFT_SUCCESS;
 }
 
 turbofft_status turbofft_set_threshold_scale(turbofft_plan* p, double factor) {
   if (!p || !(factor > 0) || !isfinite(factor)) return TURBOFFT_INVALID_VALUE;
   p->threshold_scale = factor;
+  for (auto m : p->members) m->threshold_scale = factor;
+  if (p->ragged) drop_graph(p);  // the captured launches hold the old threshold
   return TURBOFFT_SUCCESS;
 }
 
 turbofft_status turbofft_inject(turbofft_plan* p, turbofft_site site, int bit) {
   if (!p) return TURBOFFT_INVALID_VALUE;
+  if (p->ragged) {
+    if (site.transform < 0 || site.transform >= p->batch) return TURBOFFT_INVALID_VALUE;
+    turbofft_plan* m = p->members[(size_t)p->member_of[(size_t)site.transform]];
+    turbofft_site ls = site;
+    ls.transform = p->local_of[(size_t)site.transform];
+    turbofft_status st = turbofft_inject(m, ls, bit);
+    if (st == TURBOFFT_SUCCESS) p->armed_any = true;
+    return st;
+  }
   const int nbits = p->dtype == TURBOFFT_C2C_F32 ? 32 : 64;
   if (bit < 0 || bit >= nbits) return TURBOFFT_INVALID_VALUE;
   if (site.transform < 0 || site.transform >= p->batch) return TURBOFFT_INVALID_VALUE;
@@ -601,11 +1019,12 @@ turbofft_status turbofft_inject(turbofft_plan* p, turbofft_site site, int bit) {
 turbofft_status turbofft_exec(turbofft_plan* p, const void* in, void* out, turbofft_stream stream) {
   if (!p || !in || !out) return TURBOFFT_INVALID_VALUE;
   if (!aligned16(in) || !aligned16(out)) return TURBOFFT_INVALID_VALUE;
-  const size_t bytes = (size_t)(p->batch * p->n) * elem_bytes(p->dtype);
+  const size_t bytes = (size_t)(p->ragged ? p->extent : p->batch * p->n) * elem_bytes(p->dtype);
   const char* a = static_cast<const char*>(in);
   const char* b = static_cast<const char*>(out);
   if (a < b + bytes && b < a + bytes) return TURBOFFT_UNSUPPORTED;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (p->ragged) return exec_ragged(p, in, out, s);
   const bool ft = p->ft_mode != TURBOFFT_FT_OFF;
   if (ft) {
     cudaError_t e = cudaMemsetAsync(p->d_fts, 0, tf::FT_HEADER_BYTES, s);
@@ -634,6 +1053,27 @@ turbofft_status turbofft_exec_host(turbofft_plan* p, const void* host_in, void* 
   if (!p || !host_in || !host_out) return TURBOFFT_INVALID_VALUE;
   if (p->device < 0 || p->device >= 16) return TURBOFFT_UNSUPPORTED;
   const size_t eb = elem_bytes(p->dtype);
+  if (p->ragged) {
+    // one copy in, the graph, one copy out, ordered on `stream`
+    HostStage& hs = g_stage[p->device];
+    std::lock_guard<std::mutex> lock(hs.mu);
+    const size_t bytes = (size_t)p->extent * eb;
+    cudaError_t e = stage_reserve(hs, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cuda_fail(p, e, "exec_host staging");
+    }
+    cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+    if ((e = cudaMemcpyAsync(hs.in[0], host_in, bytes, cudaMemcpyHostToDevice, user)) != cudaSuccess)
+      return cuda_fail(p, e, "h2d");
+    turbofft_status st = exec_ragged(p, hs.in[0], hs.out[0], user);
+    if (st != TURBOFFT_SUCCESS) return st;
+    if ((e = cudaMemcpyAsync(host_out, hs.out[0], bytes, cudaMemcpyDeviceToHost, user)) != cudaSuccess)
+      return cuda_fail(p, e, "d2h");
+    if ((e = cudaEventRecord(p->done, user)) != cudaSuccess) return cuda_fail(p, e, "event record");
+    if ((e = cudaEventSynchronize(p->done)) != cudaSuccess) return cuda_fail(p, e, "exec_host");
+    return TURBOFFT_SUCCESS;
+  }
   const size_t per = (size_t)p->n * eb;
   // chunk: whole transforms, about 64 MiB (at least one transform)
   const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(p->batch, (int64_t)(kStageChunkBytes / per)));
@@ -703,6 +1143,7 @@ turbofft_status turbofft_exec_host(turbofft_plan* p, const void* host_in, void* 
 
 turbofft_status turbofft_set_workspace(turbofft_plan* p, void* workspace, size_t bytes) {
   if (!p) return TURBOFFT_INVALID_VALUE;
+  if (p->ragged) return TURBOFFT_UNSUPPORTED;
   if (p->num_passes == 1) return TURBOFFT_SUCCESS;  // nothing to place
   if (!workspace || bytes < p->scratch_bytes || !aligned16(workspace)) return TURBOFFT_INVALID_VALUE;
   if (p->scratch_owned) {
@@ -723,6 +1164,7 @@ turbofft_status turbofft_set_workspace(turbofft_plan* p, void* workspace, size_t
 
 turbofft_status turbofft_set_profiling(turbofft_plan* p, int enable) {
   if (!p) return TURBOFFT_INVALID_VALUE;
+  if (p->ragged) return TURBOFFT_UNSUPPORTED;
   if (enable && !p->prof_ev[0][0]) {
     for (auto& pr : p->prof_ev)
       for (auto& e : pr) {
@@ -759,29 +1201,10 @@ turbofft_status turbofft_get_report(turbofft_plan* p, turbofft_report* r) {
   if (p->ft_mode == TURBOFFT_FT_OFF || !p->have_exec) return TURBOFFT_SUCCESS;
   cudaError_t e = cudaEventSynchronize(p->done);
   if (e != cudaSuccess) return cuda_fail(p, e, "report wait");
-  const FtState& h = *p->h_fts;
-  r->groups_checked = (int64_t)h.groups;
-  r->detected = (int64_t)h.detected;
-  r->located = (int64_t)h.located;
-  r->corrected = (int64_t)h.corrected;
-  r->recomputed = (int64_t)h.recomputed;
-  r->uncorrectable = (int64_t)(h.uncorrectable + h.dropped);
-  r->max_clean_ratio = h.max_clean_ratio;
-  const int nrec = (int)std::min<unsigned long long>(h.num_records, tf::MAX_RECORDS);
-  for (int i = 0; i < nrec; ++i) {
-    const FtRecord& rc = h.rec[i];
-    if (r->first_pass < 0) {
-      r->first_pass = rc.pass_id;
-      r->first_residual = sqrt(rc.s1r * rc.s1r + rc.s1i * rc.s1i);
-      r->first_threshold = rc.tau;
-    }
-    if (rc.signal >= 0 && r->first_transform < 0) {
-      const int kind = p->pass[rc.pass_id].kind;
-      int64_t tr = rc.signal;
-      if (kind == tf::KIND_COL) tr = rc.signal / p->n2;
-      if (kind == tf::KIND_ROW) tr = rc.signal / p->n1;
-      r->first_transform = tr + rc.transform_base;
-    }
+  if (p->ragged) {
+    for (size_t k = 0; k < p->members.size(); ++k) add_report(p->members[k], &p->member_ids[k], r);
+  } else {
+    add_report(p, nullptr, r);
   }
   if (r->uncorrectable > 0) return TURBOFFT_FT_UNCORRECTABLE;
   if (p->ft_mode == TURBOFFT_FT_DETECT && r->detected > 0) return TURBOFFT_FT_UNCORRECTABLE;
@@ -795,7 +1218,7 @@ turbofft_status turbofft_get_report(turbofft_plan* p, turbofft_report* r) {
 // ---------------------------------------------------------------------------
 namespace tf {
 
-size_t plan_scratch_bytes(const turbofft_plan* p) { return p->num_passes == 2 ? p->scratch_bytes : 0; }
+size_t plan_scratch_bytes(const turbofft_plan* p) { return (!p->ragged && p->num_passes == 2) ? p->scratch_bytes : 0; }
 
 int plan_device(const turbofft_plan* p) { return p->device; }
 
@@ -803,6 +1226,7 @@ void plan_set_error(turbofft_plan* p, const char* msg) { p->last_error = msg; }
 
 turbofft_status exec_given_scratch(turbofft_plan* p, const void* in, void* out, void* scratch, cudaStream_t s) {
   if (!p || !in || !out) return TURBOFFT_INVALID_VALUE;
+  if (p->ragged) return TURBOFFT_UNSUPPORTED;
   if (!aligned16(in) || !aligned16(out)) return TURBOFFT_INVALID_VALUE;
   if (p->num_passes == 2 && (!scratch || !aligned16(scratch))) return TURBOFFT_INVALID_VALUE;
   const size_t bytes = (size_t)(p->batch * p->n) * elem_bytes(p->dtype);

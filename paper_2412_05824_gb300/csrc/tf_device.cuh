@@ -384,7 +384,15 @@ struct Geo {
   long long n;   // full transform length N
   int n1, n2;    // N = n1 * n2 (single pass: n1 = N, n2 = 1)
   long long batch;
+  // element offset of transform b in this pass's input / output, or null for
+  // the contiguous layout b * N (ragged batches index their transforms)
+  const long long* in_tab;
+  const long long* out_tab;
 };
+
+__device__ __forceinline__ long long tr_base(const long long* tab, long long b, long long n) {
+  return tab ? __ldg(tab + b) : b * n;
+}
 
 // signal id of slot `slot` of work unit `unit`; -1 if past the end (ragged tail)
 template <class K> __device__ __forceinline__ long long signal_of(const Geo& g, long long unit, int slot) {
@@ -404,30 +412,44 @@ template <class K> __device__ __forceinline__ long long signal_of(const Geo& g, 
   }
 }
 
-// element offset of position `pos` of signal `sig` in this pass's input
-template <class K> __device__ __forceinline__ long long in_off(const Geo& g, long long sig, int pos) {
+// Addressing of signal `sig`: element (pos) of its input sits at
+// in_base(sig) + pos * in_step, of its output at out_base(sig) + pos * out_step.
+//   SP:  transform sig, contiguous
+//   COL: column n2 of transform b = sig / N2 (stride N2)
+//   ROW: row k1 of transform b = sig / N1: input contiguous, output stride N1
+template <class K> __device__ __forceinline__ long long in_base(const Geo& g, long long sig) {
   if constexpr (K::KIND == KIND_SP) {
-    return sig * g.n + pos;
+    return tr_base(g.in_tab, sig, g.n);
   } else if constexpr (K::KIND == KIND_COL) {
-    long long b = sig / g.n2;
-    int n2 = (int)(sig - b * g.n2);
-    return b * g.n + (long long)pos * g.n2 + n2;
+    const long long b = sig / g.n2;
+    return tr_base(g.in_tab, b, g.n) + (sig - b * g.n2);
   } else {
-    long long b = sig / g.n1;
-    int k1 = (int)(sig - b * g.n1);
-    return b * g.n + (long long)k1 * g.n2 + pos;
+    const long long b = sig / g.n1;
+    return tr_base(g.in_tab, b, g.n) + (sig - b * g.n1) * g.n2;
   }
 }
-
-// element offset of output position `pos` of signal `sig` in this pass's output
-template <class K> __device__ __forceinline__ long long out_off(const Geo& g, long long sig, int pos) {
-  if constexpr (K::KIND == KIND_ROW) {
-    long long b = sig / g.n1;
-    int k1 = (int)(sig - b * g.n1);
-    return b * g.n + k1 + (long long)g.n1 * pos;
+template <class K> __device__ __forceinline__ long long in_step(const Geo& g) {
+  return K::KIND == KIND_COL ? (long long)g.n2 : 1;
+}
+template <class K> __device__ __forceinline__ long long out_base(const Geo& g, long long sig) {
+  if constexpr (K::KIND == KIND_SP) {
+    return tr_base(g.out_tab, sig, g.n);
+  } else if constexpr (K::KIND == KIND_COL) {
+    const long long b = sig / g.n2;
+    return tr_base(g.out_tab, b, g.n) + (sig - b * g.n2);
   } else {
-    return in_off<K>(g, sig, pos);
+    const long long b = sig / g.n1;
+    return tr_base(g.out_tab, b, g.n) + (sig - b * g.n1);
   }
+}
+template <class K> __device__ __forceinline__ long long out_step(const Geo& g) {
+  return K::KIND == KIND_SP ? 1 : (K::KIND == KIND_COL ? (long long)g.n2 : (long long)g.n1);
+}
+template <class K> __device__ __forceinline__ long long in_off(const Geo& g, long long sig, int pos) {
+  return in_base<K>(g, sig) + (long long)pos * in_step<K>(g);
+}
+template <class K> __device__ __forceinline__ long long out_off(const Geo& g, long long sig, int pos) {
+  return out_base<K>(g, sig) + (long long)pos * out_step<K>(g);
 }
 
 // inter-pass twiddle w_N^{k1 * n2} for column n2 of signal `sig` (KIND_COL):
@@ -593,14 +615,25 @@ __device__ __forceinline__ void issue_unit(const PassArgs<typename K::real>& A, 
     const long long first = unit * K::S;
     long long nv = g.batch - first;
     if (nv > K::S) nv = K::S;
-    const char* src = reinterpret_cast<const char*>(A.in + first * K::NS);
-    const int chunks = (int)(nv * K::NS * (long long)sizeof(c) / 16);
-    for (int q = tid; q < chunks; q += K::NT) cp_async16(stage + 16 * q, src + 16 * (size_t)q);
+    if (g.in_tab == nullptr) {
+      const char* src = reinterpret_cast<const char*>(A.in + first * K::NS);
+      const int chunks = (int)(nv * K::NS * (long long)sizeof(c) / 16);
+      for (int q = tid; q < chunks; q += K::NT) cp_async16(stage + 16 * q, src + 16 * (size_t)q);
+    } else {
+      // indexed transforms: one contiguous run per slot
+      constexpr int cps = K::NS * (int)sizeof(c) / 16;  // 16-byte chunks per transform
+      const int chunks = (int)nv * cps;
+      for (int q = tid; q < chunks; q += K::NT) {
+        const int sl = q / cps, j = q - sl * cps;
+        const char* src = reinterpret_cast<const char*>(A.in + __ldg(g.in_tab + first + sl));
+        cp_async16(stage + (size_t)sl * K::NS * sizeof(c) + 16 * j, src + 16 * (size_t)j);
+      }
+    }
   } else if constexpr (K::KIND == KIND_ROW) {
     const int blocks = g.n1 / K::S;
     const long long b = unit / blocks;
     const int r0 = (int)(unit - b * blocks) * K::S;
-    const char* src = reinterpret_cast<const char*>(A.in + b * g.n + (long long)r0 * g.n2);
+    const char* src = reinterpret_cast<const char*>(A.in + tr_base(g.in_tab, b, g.n) + (long long)r0 * g.n2);
     constexpr int chunks = K::S * K::NS * (int)sizeof(c) / 16;
     for (int q = tid; q < chunks; q += K::NT) cp_async16(stage + 16 * q, src + 16 * (size_t)q);
   } else {
@@ -609,7 +642,7 @@ __device__ __forceinline__ void issue_unit(const PassArgs<typename K::real>& A, 
     const int c0 = (int)(unit - b * blocks) * K::S;
     constexpr int cpr = K::S * (int)sizeof(c) / 16;  // 16-byte chunks per row of the tile
     static_assert(cpr >= 1, "a column tile row must span 16 bytes");
-    const c* base = A.in + b * g.n + c0;
+    const c* base = A.in + tr_base(g.in_tab, b, g.n) + c0;
     constexpr int chunks = K::NS * cpr;
     for (int q = tid; q < chunks; q += K::NT) {
       const int p = q / cpr, j = q - p * cpr;
@@ -822,19 +855,23 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
       __syncthreads();
       const int s2 = tid % S, t2 = tid / S;
       const long long sig2 = signal_of<K>(g, unit, s2);
+      c* const ob = A.out + out_base<K>(g, sig2);
+      const long long os = out_step<K>(g);
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         const int pos = t2 + i * P;
         const c v = conj_mask(sm[s2 * K::NS + (pos ^ (s2 & ((1 << K::B) - 1)))], mask_out);
-        __stcs(A.out + out_off<K>(g, sig2, pos), v);  // streaming: keep L1 for the tables
+        __stcs(ob + pos * os, v);  // streaming: keep L1 for the tables
       }
       __syncthreads();
     } else {
       if (valid) {
+        c* const ob = A.out + out_base<K>(g, sig);
+        const long long os = out_step<K>(g);
 #pragma unroll
         for (int i = 0; i < E; ++i) {
           const c v = conj_mask(a[i], mask_out);
-          __stcs(A.out + out_off<K>(g, sig, t + i * P), v);
+          __stcs(ob + (t + i * P) * os, v);
         }
       }
     }

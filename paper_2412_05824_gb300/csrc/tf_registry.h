@@ -32,5 +32,8 @@ const KernelEntry* entries_f32_row(int* count);
 const KernelEntry* entries_f64_sp(int* count);
 const KernelEntry* entries_f64_col(int* count);
 const KernelEntry* entries_f64_row(int* count);
+// alternative shapes (registered after the defaults)
+const KernelEntry* entries_f32_alt_sp(int* count);
+const KernelEntry* entries_f32_alt_cr(int* count);
 
 }  // namespace tf

@@ -42,6 +42,8 @@ __all__ = [
     "tone",
     "structured",
     "uniform_complex_torch",
+    "ragged_sizes",
+    "ragged_offsets",
 ]
 
 
@@ -106,6 +108,30 @@ def normal_complex(seed: int, batch: int, n: int, dtype=np.float32) -> np.ndarra
 
 def _ctype(dtype):
     return np.complex64 if np.dtype(dtype) == np.float32 else np.complex128
+
+
+def ragged_sizes(seed: int, count: int, lo_log: int = 6, hi_log: int = 16) -> np.ndarray:
+    """Transform sizes 2^k with k drawn uniformly from [lo_log, hi_log]
+    (log-uniform over the powers of two), as int64.  k = lo_log +
+    floor(hi32(word(i)) * m / 2^32), m = hi_log - lo_log + 1."""
+    m = np.uint64(hi_log - lo_log + 1)
+    w = splitmix_words(seed, 0, count)
+    k = ((w >> np.uint64(32)) * m) >> np.uint64(32)
+    return (np.int64(1) << (k.astype(np.int64) + lo_log)).astype(np.int64)
+
+
+def ragged_offsets(sizes, seed: int | None = None, max_gap: int = 0) -> tuple[np.ndarray, int]:
+    """Element offsets of transforms packed in order; with a seed, an even gap
+    in [0, max_gap) precedes each transform (gaps keep every start 16-byte
+    aligned for complex64).  Returns (offsets int64, total span)."""
+    sizes = np.asarray(sizes, dtype=np.int64)
+    gaps = np.zeros(len(sizes), dtype=np.int64)
+    if seed is not None and max_gap > 1:
+        w = splitmix_words(seed, 0, len(sizes))
+        gaps = 2 * ((w >> np.uint64(33)) % np.uint64(max_gap // 2)).astype(np.int64)
+    ends = np.cumsum(gaps + sizes)
+    offsets = ends - sizes
+    return offsets.astype(np.int64), int(ends[-1]) if len(sizes) else 0
 
 
 def impulse(batch: int, n: int, dtype=np.float32, position: int = 0) -> np.ndarray:

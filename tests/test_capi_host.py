@@ -82,3 +82,47 @@ def test_no_gpu_reports_cuda_error_not_crash(L):
     h = ctypes.c_void_p()
     st = L.turbofft_plan_create(64, 4, 0, -1, 0, ctypes.byref(h))
     assert st == tfl.CUDA_ERROR and not h.value
+
+
+def _ragged(L, sizes, offsets, dtype=0, direction=-1, ft=0, count=None):
+    arr = ctypes.c_int64 * max(1, len(sizes))
+    h = ctypes.c_void_p(123)
+    st = L.turbofft_plan_create_ragged(arr(*sizes), arr(*offsets), len(sizes) if count is None else count,
+                                       dtype, direction, ft, ctypes.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("sizes,offsets,dtype,direction,ft,count", [
+    ([64, 128], [0, 64], 0, -1, 0, 0),          # empty batch
+    ([64, 96], [0, 64], 0, -1, 0, None),        # not a power of two
+    ([64, 4], [0, 64], 0, -1, 0, None),         # below the minimum length 8
+    ([64, 1 << 25], [0, 64], 0, -1, 0, None),   # above the maximum length
+    ([64, 128], [0, -2], 0, -1, 0, None),       # negative offset
+    ([64, 128], [0, 65], 0, -1, 0, None),       # odd complex64 offset: not 16-byte aligned
+    ([64, 128], [0, 32], 0, -1, 0, None),       # overlapping transforms
+    ([128, 64], [40, 0], 0, -1, 0, None),       # overlap found after sorting by offset
+    ([64, 128], [0, 64], 3, -1, 0, None),       # bad dtype
+    ([64, 128], [0, 64], 0, 5, 0, None),        # bad direction
+    ([64, 128], [0, 64], 0, -1, 8, None),       # bad ft mode
+])
+def test_ragged_create_rejects_bad_arguments(L, sizes, offsets, dtype, direction, ft, count):
+    st, h = _ragged(L, sizes, offsets, dtype, direction, ft, count)
+    assert st == tfl.INVALID_VALUE
+    assert not h.value
+
+
+def test_ragged_null_arrays_are_rejected(L):
+    h = ctypes.c_void_p(123)
+    assert L.turbofft_plan_create_ragged(None, None, 3, 0, -1, 0, ctypes.byref(h)) == tfl.INVALID_VALUE
+    assert L.turbofft_plan_get_member_info(None, 0, None) == tfl.INVALID_VALUE
+    assert L.turbofft_set_autotune(0) == tfl.SUCCESS
+
+
+def test_ragged_odd_offset_is_fine_for_complex128(L):
+    # every complex128 element is 16 bytes: any offset is aligned; without a
+    # GPU the call gets as far as the device query
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    st, h = _ragged(L, [64, 128], [1, 65], dtype=1)
+    assert st == tfl.CUDA_ERROR and not h.value
