@@ -120,10 +120,12 @@ class ClockSampler:
 
 
 def src_hash():
+    """Hash of the device code (kernel headers and kernel translation units);
+    host-side files do not change what a kernel moves."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2412_05824_gb300", "csrc")
     for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
+        if f.endswith(".cuh") or f in ("tf_types.h", "tf_dft_constants.h") or (f.startswith("tf_k_") and f.endswith(".cu")):
             h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 

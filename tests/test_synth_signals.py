@@ -48,3 +48,29 @@ def test_structured_inputs():
     np.testing.assert_allclose(np.abs(t), 1.0, atol=1e-15)
     assert ss.impulse(2, 8)[0, 0] == 1 and np.count_nonzero(ss.impulse(2, 8)) == 2
     assert np.all(ss.constant(1, 8) == 1)
+
+
+def test_ragged_sizes_are_log_uniform_powers_of_two():
+    s = ss.ragged_sizes(7, 22000, 6, 16)
+    assert s.dtype == np.int64 and len(s) == 22000
+    vals, counts = np.unique(s, return_counts=True)
+    assert list(vals) == [1 << k for k in range(6, 17)]
+    # 2000 expected per size; a 5-sigma band of the binomial
+    assert np.all(np.abs(counts - 2000) < 5 * np.sqrt(2000))
+    assert np.array_equal(s, ss.ragged_sizes(7, 22000, 6, 16))
+    assert not np.array_equal(s, ss.ragged_sizes(8, 22000, 6, 16))
+    # a prefix of a longer draw is the shorter draw (counter-based)
+    assert np.array_equal(s[:100], ss.ragged_sizes(7, 100, 6, 16))
+
+
+def test_ragged_offsets_pack_without_overlap():
+    sizes = ss.ragged_sizes(3, 500, 3, 12)
+    offs, total = ss.ragged_offsets(sizes)
+    assert offs[0] == 0 and total == int(sizes.sum())
+    assert np.array_equal(offs[1:], np.cumsum(sizes)[:-1])
+    offs, total = ss.ragged_offsets(sizes, seed=9, max_gap=64)
+    assert np.all(offs % 2 == 0)  # complex64 starts stay 16-byte aligned
+    assert np.all(offs[1:] >= offs[:-1] + sizes[:-1])
+    assert total == int(offs[-1] + sizes[-1]) and total >= int(sizes.sum())
+    gaps = offs - np.concatenate([[0], offs[:-1] + sizes[:-1]])
+    assert gaps.max() < 64 and gaps.max() > 0
