@@ -119,14 +119,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def src_hash():
-    """Hash of the device code (kernel headers and kernel translation units);
-    host-side files do not change what a kernel moves."""
+KERNEL_HEADERS = ("tf_device.cuh", "tf_types.h", "tf_dft_constants.h", "tf_instantiate.cuh", "tf_registry.h")
+
+
+def src_hash(key=None):
+    """Hash of the device code one kernel is built from: the shared kernel
+    headers and, for a key like float64_col_n2048_ft, its translation unit."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2412_05824_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith(".cuh") or f in ("tf_types.h", "tf_dft_constants.h") or (f.startswith("tf_k_") and f.endswith(".cu")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    files = list(KERNEL_HEADERS)
+    if key:
+        dt, kind = key.split("_")[:2]
+        files.append("tf_k_%s_%s.cu" % ("f32" if dt == "float32" else "f64", kind))
+    for f in files:
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -139,7 +145,7 @@ def ncu_traffic(key):
     except (OSError, ValueError):
         return None
     ent = t.get(key)
-    if ent and ent.get("src_hash") == src_hash():
+    if ent and ent.get("src_hash") == src_hash(key):
         return ent.get("traffic_bytes_per_launch")
     return None
 
