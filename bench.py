@@ -131,6 +131,8 @@ def src_hash(key=None):
     if key:
         dt, kind = key.split("_")[:2]
         files.append("tf_k_%s_%s.cu" % ("f32" if dt == "float32" else "f64", kind))
+        if kind == "cl":
+            files += ["tf_cluster.cuh", "tf_instantiate_cl.cuh"]
     for f in files:
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
@@ -522,9 +524,12 @@ def run_ours(args):
         inf = pl.info()
         for (ps, corr, msk) in pl.kernel_times():
             kind = "fix" if corr else ("sp" if inf["num_passes"] == 1 else ("col" if ps == 0 else "row"))
-            key = "%s_%s_n%d_ft" % (dt2, kind, inf["sub_n"][ps])
+            sub = inf["sub_n"][ps]
+            if inf["cluster"] and not corr:
+                kind, sub = "cl", n2  # both phases in one cluster kernel
+            key = "%s_%s_n%d_ft" % (dt2, kind, sub)
             kernel_ms[key] = kernel_ms.get(key, 0.0) + msk
-            kernel_launch.setdefault(key, []).append((msk, eb2, inf["sub_n"][ps]))
+            kernel_launch.setdefault(key, []).append((msk, eb2, sub))
             step_kernel_total += msk
         pl.set_profiling(False)
     kname = max((k for k in kernel_ms if not k.split("_")[1] == "fix"), key=lambda k: kernel_ms[k])
@@ -589,7 +594,8 @@ def run_ours(args):
 
     launches_per_step = 0
     for dt2, eb2, d2, n2 in cfgs:
-        launches_per_step += plans_ft[(dt2, d2, n2)].info()["num_passes"] * 2
+        inf2 = plans_ft[(dt2, d2, n2)].info()
+        launches_per_step += 2 if inf2["cluster"] else inf2["num_passes"] * 2
     sweep = []
     for i, (dt2, eb2, d2, n2) in enumerate(cfgs):
         b = 2.0 * ELEMENTS * eb2

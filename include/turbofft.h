@@ -139,6 +139,10 @@ typedef struct {
   int32_t per_block[2];     /* transforms (SP) / columns / rows one block holds per transaction */
   int32_t num_members;      /* ragged plan: distinct sizes (member plans); 0 otherwise */
   int32_t autotuned;        /* 1 if launch shapes were chosen by timing (turbofft_set_autotune) */
+  int32_t cluster;          /* > 0: both passes run in ONE kernel whose thread-block clusters of
+                               this many blocks share each transform (one HBM round trip);
+                               grid/block then describe that kernel */
+  int32_t reserved2;
 } turbofft_plan_info;
 
 /* Duration of one kernel of the last exec (turbofft_set_profiling). */
@@ -165,6 +169,25 @@ typedef struct {
 turbofft_status turbofft_plan_create(int64_t n, int64_t batch, turbofft_dtype dtype,
                                      int direction, turbofft_ft_mode ft_mode,
                                      turbofft_plan **plan);
+
+/*
+ * Same as turbofft_plan_create with the plan's structure fixed instead of
+ * chosen (by default, or by timing when autotuning is on):
+ *   TURBOFFT_STRUCTURE_SPLIT    one kernel pass for n up to the largest
+ *                               single-block size (2^13 float32, 2^12
+ *                               float64), two four-step passes beyond it
+ *   TURBOFFT_STRUCTURE_CLUSTER  one kernel pass whose thread-block clusters
+ *                               share each transform (info.cluster > 0);
+ *                               TURBOFFT_UNSUPPORTED for sizes without a
+ *                               cluster configuration
+ * Every structure computes the same transform to the same accuracy bar.
+ * Errors: as turbofft_plan_create; INVALID_VALUE for another structure.
+ */
+#define TURBOFFT_STRUCTURE_SPLIT 1
+#define TURBOFFT_STRUCTURE_CLUSTER 2
+turbofft_status turbofft_plan_create_structured(int64_t n, int64_t batch, turbofft_dtype dtype,
+                                                int direction, turbofft_ft_mode ft_mode, int structure,
+                                                turbofft_plan **plan);
 
 /*
  * Ragged batch: `count` transforms of mixed power-of-two lengths in one plan

@@ -41,6 +41,9 @@ FT_CORRECT_REGISTERS = 3
 _DIRS = {"forward": FORWARD, "inverse": INVERSE, "inverse_unscaled": INVERSE_UNSCALED,
          "forward_scaled": FORWARD_SCALED, FORWARD: FORWARD, INVERSE: INVERSE,
          INVERSE_UNSCALED: INVERSE_UNSCALED, FORWARD_SCALED: FORWARD_SCALED}
+STRUCTURE_SPLIT = 1
+STRUCTURE_CLUSTER = 2
+_STRUCT = {"split": STRUCTURE_SPLIT, "cluster": STRUCTURE_CLUSTER}
 _FT = {"off": FT_OFF, "detect": FT_DETECT, "correct": FT_CORRECT, "correct_registers": FT_CORRECT_REGISTERS,
        None: FT_OFF, False: FT_OFF, FT_OFF: FT_OFF, FT_DETECT: FT_DETECT, FT_CORRECT: FT_CORRECT,
        FT_CORRECT_REGISTERS: FT_CORRECT_REGISTERS}
@@ -68,7 +71,8 @@ class PlanInfo(ctypes.Structure):
                 ("group_transactions", ctypes.c_int32), ("grid", ctypes.c_int32 * 2),
                 ("block", ctypes.c_int32 * 2), ("workspace_bytes", ctypes.c_int64),
                 ("scratch_bytes", ctypes.c_int64), ("per_block", ctypes.c_int32 * 2),
-                ("num_members", ctypes.c_int32), ("autotuned", ctypes.c_int32)]
+                ("num_members", ctypes.c_int32), ("autotuned", ctypes.c_int32),
+                ("cluster", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
 
 class KernelTime(ctypes.Structure):
@@ -81,7 +85,7 @@ EXPORTS = [
     "turbofft_destroy", "turbofft_status_string", "turbofft_last_error",
     "turbofft_set_workspace", "turbofft_set_profiling", "turbofft_get_kernel_times",
     "turbofft_exec_static_scratch", "turbofft_plan_create_ragged", "turbofft_plan_get_member_info",
-    "turbofft_set_autotune",
+    "turbofft_set_autotune", "turbofft_plan_create_structured",
 ]
 
 STATIC_SCRATCH_BYTES = 32 << 20
@@ -106,6 +110,7 @@ def lib() -> ctypes.CDLL:
                                               ctypes.POINTER(vp)]
     L.turbofft_plan_get_member_info.argtypes = [vp, i32, ctypes.POINTER(PlanInfo)]
     L.turbofft_set_autotune.argtypes = [i32]
+    L.turbofft_plan_create_structured.argtypes = [i64, i64, i32, i32, i32, i32, ctypes.POINTER(vp)]
     L.turbofft_inject.argtypes = [vp, Site, i32]
     L.turbofft_get_report.argtypes = [vp, ctypes.POINTER(Report)]
     L.turbofft_plan_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
@@ -150,14 +155,23 @@ def _dtype_code(dtype) -> int:
 class Plan:
     """A turbofft plan: batch transforms of length n (owns its device tables)."""
 
-    def __init__(self, n: int, batch: int, dtype="complex64", direction="forward", ft="off"):
+    def __init__(self, n: int, batch: int, dtype="complex64", direction="forward", ft="off",
+                 structure="default"):
+        """structure: "default" (chosen by the library), "split" (one pass or
+        two four-step passes) or "cluster" (one pass over thread-block
+        clusters)."""
         self.n, self.batch = int(n), int(batch)
         self.dtype_code = _dtype_code(dtype)
         self.direction = _DIRS[direction]
         self.ft_mode = _FT[ft]
         h = ctypes.c_void_p()
-        _check(lib().turbofft_plan_create(self.n, self.batch, self.dtype_code, self.direction,
-                                          self.ft_mode, ctypes.byref(h)), "turbofft_plan_create")
+        if structure == "default":
+            _check(lib().turbofft_plan_create(self.n, self.batch, self.dtype_code, self.direction,
+                                              self.ft_mode, ctypes.byref(h)), "turbofft_plan_create")
+        else:
+            _check(lib().turbofft_plan_create_structured(self.n, self.batch, self.dtype_code, self.direction,
+                                                         self.ft_mode, _STRUCT[structure], ctypes.byref(h)),
+                   "turbofft_plan_create_structured")
         self._h = h
 
     @property

@@ -23,12 +23,14 @@
 #include <vector>
 
 #include "../../include/turbofft.h"
+#include "tf_cluster.cuh"
 #include "tf_device.cuh"
 #include "tf_internal.h"
 #include "tf_registry.h"
 
 using tf::FtRecord;
 using tf::FtState;
+using tf::ClEntry;
 using tf::KernelEntry;
 
 namespace {
@@ -38,7 +40,14 @@ namespace {
 // ---------------------------------------------------------------------------
 struct Registry {
   std::vector<const KernelEntry*> all;
+  std::vector<const ClEntry*> cl;
   Registry() {
+    tf::ClTableFn cfns[] = {tf::entries_f32_cl};
+    for (auto fn : cfns) {
+      int n = 0;
+      const ClEntry* t = fn(&n);
+      for (int i = 0; i < n; ++i) cl.push_back(&t[i]);
+    }
     tf::EntryTableFn fns[] = {tf::entries_f32_sp, tf::entries_f32_col, tf::entries_f32_row,
                               tf::entries_f64_sp, tf::entries_f64_col, tf::entries_f64_row,
                               tf::entries_f32_alt_sp, tf::entries_f32_alt_cr};
@@ -60,6 +69,11 @@ struct Registry {
     for (auto e : all)
       if (e->dtype == dtype && e->kind == kind && e->ns == ns) v.push_back(e);
     return v;
+  }
+  const ClEntry* find_cl(int dtype, int64_t n) const {
+    for (auto e : cl)
+      if (e->dtype == dtype && e->n == n) return e;
+    return nullptr;
   }
   int max_sp(int dtype) const {
     int m = 0;
@@ -216,6 +230,9 @@ struct turbofft_plan {
   std::vector<int32_t> member_of;  // ragged: member plan of each global transform
   std::vector<int64_t> local_of;   // ragged: index of each global transform within its member
   bool autotuned = false;          // launch shapes chosen by timing (turbofft_set_autotune)
+  // single-pass cluster plan: both four-step phases in one kernel
+  const ClEntry* cl = nullptr;
+  int cl_grid = 0;
 };
 
 namespace {
@@ -323,7 +340,7 @@ void fill_args(const turbofft_plan* p, int pi, const void* in, void* out, int64_
   A.geo.batch = batch;
   A.geo.in_tab = (pi == 0) ? p->d_tab : nullptr;
   A.geo.out_tab = (pi == p->num_passes - 1) ? p->d_tab : nullptr;
-  A.num_units = units_for(p, pi, batch);
+  A.num_units = p->cl ? batch : units_for(p, pi, batch);  // cluster plans: one unit per transform
   const bool inverse = p->direction > 0;
   const bool scaled = p->direction == TURBOFFT_INVERSE || p->direction == TURBOFFT_FORWARD_SCALED;
   const bool last = (pi == p->num_passes - 1);
@@ -342,9 +359,55 @@ void fill_args(const turbofft_plan* p, int pi, const void* in, void* out, int64_
 }
 
 // queue one transform of `batch` transforms (device pointers) on `stream`
+template <typename R>
+void fill_cl_args(const turbofft_plan* p, const void* in, void* out, int64_t batch, int64_t tbase,
+                  const tf::InjectSite& inj, tf::ClArgs<R>& A) {
+  typedef typename tf::CT<R>::c c;
+  fill_args<R>(p, 0, in, out, batch, tbase, inj, A.p);
+  const bool inverse = p->direction > 0;
+  const bool scaled = p->direction == TURBOFFT_INVERSE || p->direction == TURBOFFT_FORWARD_SCALED;
+  A.p.geo.out_tab = p->d_tab;
+  A.p.conj_out = inverse ? 1 : 0;
+  A.p.out_scale = scaled ? (R)(1.0 / (double)p->n) : (R)1;
+  A.p.num_units = batch;
+  A.twB = static_cast<const c*>(p->pass[1].d_tw);
+  A.evB = static_cast<const c*>(p->pass[1].d_ev);
+  A.vvB = static_cast<const c*>(p->pass[1].d_vv);
+}
+
+// cluster kernels have no register-sums variant: that mode runs as CORRECT
+int cl_variant(int ft_mode) { return ft_mode == TURBOFFT_FT_OFF ? 0 : 1; }
+
 turbofft_status run(turbofft_plan* p, const void* in, void* out, void* scratch, int64_t batch, int64_t tbase,
                     cudaStream_t stream, const tf::InjectSite& inj) {
   const bool ft = p->ft_mode != TURBOFFT_FT_OFF;
+  if (p->cl) {
+    const ClEntry* ce = p->cl;
+    const int grid = (int)std::min<long long>((long long)p->cl_grid, (long long)batch * ce->cluster);
+    auto timed = [&](int kind, auto&& launch) {
+      const bool prof = p->profiling && p->nprof < 8;
+      if (prof) cudaEventRecord(p->prof_ev[p->nprof][0], stream);
+      launch();
+      if (prof) {
+        cudaEventRecord(p->prof_ev[p->nprof][1], stream);
+        p->prof_kind[p->nprof++] = kind;
+      }
+    };
+    if (p->dtype == TURBOFFT_C2C_F32) {
+      tf::ClArgs<float> A;
+      fill_cl_args<float>(p, in, out, batch, tbase, inj, A);
+      timed(0, [&] { ce->main[cl_variant(p->ft_mode)](&A, grid, stream); });
+      if (ft) timed(1, [&] { ce->fix(&A, ce->cluster, stream); });
+    } else {
+      tf::ClArgs<double> A;
+      fill_cl_args<double>(p, in, out, batch, tbase, inj, A);
+      timed(0, [&] { ce->main[cl_variant(p->ft_mode)](&A, grid, stream); });
+      if (ft) timed(1, [&] { ce->fix(&A, ce->cluster, stream); });
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(p, e, "kernel launch");
+    return TURBOFFT_SUCCESS;
+  }
   for (int pi = 0; pi < p->num_passes; ++pi) {
     const PassPlan& pp = p->pass[pi];
     const void* pin = (pi == 0) ? in : scratch;
@@ -461,6 +524,10 @@ bool use_entry(turbofft_plan* p, int pi, const KernelEntry* ke) {
 // time each candidate of each pass on (in, out, scratch), which span the
 // plan's buffers; keeps the default shape of a pass whose candidates all fail
 void autotune(turbofft_plan* p, const void* in, void* out, void* scratch) {
+  if (p->cl) {  // one shape per cluster configuration
+    p->autotuned = true;
+    return;
+  }
   const Registry& reg = registry();
   const int dt = p->dtype == TURBOFFT_C2C_F32 ? 0 : 1;
   cudaStream_t s = nullptr;
@@ -525,19 +592,55 @@ void autotune(turbofft_plan* p, const void* in, void* out, void* scratch) {
   p->autotuned = true;
 }
 
-// autotune a contiguous plan on temporary buffers of its own size (nothing
-// is tuned if they cannot be allocated)
-void autotune_with_temp(turbofft_plan* p) {
+std::map<TuneKey, int> g_structure_cache;  // 1 split, 2 cluster
+
+// run f(in, out, scratch) on temporary buffers of a contiguous plan's size,
+// the input filled with a finite, non-zero pattern (0x3c bytes) so that
+// timing sees ordinary arithmetic; nothing runs if they cannot be allocated
+template <class F> void with_temp(turbofft_plan* p, F&& f) {
   const size_t bytes = (size_t)(p->batch * p->n) * elem_bytes(p->dtype);
   void *a = nullptr, *b = nullptr, *c = nullptr;
   bool ok = cudaMalloc(&a, bytes) == cudaSuccess && cudaMalloc(&b, bytes) == cudaSuccess &&
-            (p->num_passes == 1 || cudaMalloc(&c, p->scratch_bytes) == cudaSuccess);
-  // a finite, non-zero pattern (0x3c bytes) so that timing sees ordinary arithmetic
+            (p->scratch_bytes == 0 || cudaMalloc(&c, p->scratch_bytes) == cudaSuccess);
   if (ok) ok = cudaMemset(a, 0x3c, bytes) == cudaSuccess;
-  if (ok) autotune(p, a, b, c);
+  if (ok) f(a, b, c);
   cudaGetLastError();
   for (void* q : {a, b, c})
     if (q) cudaFree(q);
+}
+
+void autotune_with_temp(turbofft_plan* p) {
+  with_temp(p, [&](void* a, void* b, void* c) { autotune(p, a, b, c); });
+}
+
+// best of three execs in ms (0 if timing failed)
+double time_with_temp(turbofft_plan* p) {
+  double best = 0;
+  with_temp(p, [&](void* a, void* b, void* c) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess && cudaEventCreate(&e0) == cudaSuccess &&
+        cudaEventCreate(&e1) == cudaSuccess) {
+      const tf::InjectSite none{};
+      bool ok = queue_plan(p, a, b, c, s, none) == TURBOFFT_SUCCESS;
+      for (int rep = 0; ok && rep < 3; ++rep) {
+        ok = cudaEventRecord(e0, s) == cudaSuccess && queue_plan(p, a, b, c, s, none) == TURBOFFT_SUCCESS &&
+             cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+        float ms = 0.f;
+        if (ok) ok = cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+        if (ok && (rep == 0 || ms < best)) best = ms;
+      }
+      if (!ok) best = 0;
+      cudaStreamSynchronize(s);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    cudaGetLastError();
+    if (p->d_fts) cudaMemset(p->d_fts, 0, sizeof(FtState));
+    if (p->h_fts) memset(p->h_fts, 0, sizeof(FtState));
+  });
+  return best;
 }
 
 // ---------------------------------------------------------------------------
@@ -592,7 +695,7 @@ turbofft_status capture_ragged(turbofft_plan* p, const void* in, void* out) {
 
 turbofft_status exec_ragged(turbofft_plan* p, const void* in, void* out, cudaStream_t s) {
   for (auto m : p->members)
-    if (m->num_passes == 2 && !m->d_scratch) {
+    if (m->scratch_bytes > 0 && !m->d_scratch) {
       if (!dev_alloc(m, &m->d_scratch, m->scratch_bytes)) return TURBOFFT_ALLOC_FAILED;
       m->scratch_owned = true;
     }
@@ -643,9 +746,9 @@ void add_report(const turbofft_plan* m, const std::vector<int64_t>* ids, turboff
     }
     if (rc.signal >= 0 && r->first_transform < 0) {
       const int kind = m->pass[rc.pass_id].kind;
-      int64_t tr = rc.signal;
-      if (kind == tf::KIND_COL) tr = rc.signal / m->n2;
-      if (kind == tf::KIND_ROW) tr = rc.signal / m->n1;
+      int64_t tr = rc.signal;  // cluster plans record the transform itself
+      if (!m->cl && kind == tf::KIND_COL) tr = rc.signal / m->n2;
+      if (!m->cl && kind == tf::KIND_ROW) tr = rc.signal / m->n1;
       tr += rc.transform_base;
       r->first_transform = (ids && tr >= 0 && tr < (int64_t)ids->size()) ? (*ids)[tr] : tr;
     }
@@ -670,6 +773,21 @@ void fill_info(const turbofft_plan* p, turbofft_plan_info* info) {
     return;
   }
   info->num_passes = p->num_passes;
+  if (p->cl) {
+    const ClEntry* ce = p->cl;
+    info->cluster = ce->cluster;
+    for (int pi = 0; pi < 2; ++pi) {
+      info->sub_n[pi] = p->pass[pi].ns;
+      info->stages[pi] = pi == 0 ? ce->stages_a : ce->stages_b;
+      info->radix[pi] = ce->e;
+      info->grid[pi] = p->cl_grid;
+      info->block[pi] = ce->nt;
+      info->per_block[pi] = pi == 0 ? ce->sa : ce->sb;
+    }
+    info->workspace_bytes = p->workspace_bytes;
+    info->scratch_bytes = 0;
+    return;
+  }
   for (int pi = 0; pi < p->num_passes; ++pi) {
     info->sub_n[pi] = p->pass[pi].ns;
     info->stages[pi] = p->pass[pi].ke->stages;
@@ -729,8 +847,9 @@ turbofft_status turbofft_destroy(turbofft_plan* p) {
   return TURBOFFT_SUCCESS;
 }
 
-turbofft_status turbofft_plan_create(int64_t n, int64_t batch, turbofft_dtype dtype, int direction,
-                                     turbofft_ft_mode ft_mode, turbofft_plan** out) {
+// structure: 0 = default, 1 = single pass or two passes, 2 = cluster single pass
+static turbofft_status create_plan(int64_t n, int64_t batch, turbofft_dtype dtype, int direction,
+                                   turbofft_ft_mode ft_mode, int structure, turbofft_plan** out) {
   if (!out) return TURBOFFT_INVALID_VALUE;
   *out = nullptr;
   const int logn = ilog2_exact(n);
@@ -745,8 +864,7 @@ turbofft_status turbofft_plan_create(int64_t n, int64_t batch, turbofft_dtype dt
     return TURBOFFT_INVALID_VALUE;
 
   int dev = 0;
-  cudaError_t ce = cudaGetDevice(&dev);
-  if (ce != cudaSuccess) {
+  if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
     return TURBOFFT_CUDA_ERROR;
   }
@@ -765,7 +883,18 @@ turbofft_status turbofft_plan_create(int64_t n, int64_t batch, turbofft_dtype dt
   const int dt = dtype == TURBOFFT_C2C_F32 ? 0 : 1;
 
   // pass split: one pass up to the largest single-pass size, else N1 x N2
-  if (n <= reg.max_sp(dt)) {
+  // passes; the cluster single pass when asked for (or chosen by timing)
+  const ClEntry* ce = reg.find_cl(dt, n);
+  if (ce && structure == 2) {
+    p->cl = ce;
+    p->num_passes = 2;
+    p->n1 = ce->n1;
+    p->n2 = ce->n2;
+    p->pass[0].kind = tf::KIND_COL;
+    p->pass[0].ns = ce->n1;
+    p->pass[1].kind = tf::KIND_ROW;
+    p->pass[1].ns = ce->n2;
+  } else if (n <= reg.max_sp(dt)) {
     p->num_passes = 1;
     p->n1 = (int)n;
     p->n2 = 1;
@@ -780,7 +909,41 @@ turbofft_status turbofft_plan_create(int64_t n, int64_t batch, turbofft_dtype dt
     p->pass[1].kind = tf::KIND_ROW;
     p->pass[1].ns = p->n2;
   }
-  for (int pi = 0; pi < p->num_passes; ++pi) {
+  for (int pi = 0; pi < p->num_passes && p->cl; ++pi) {
+    if (!upload_tables(p, p->pass[pi])) {
+      turbofft_destroy(p);
+      return TURBOFFT_ALLOC_FAILED;
+    }
+  }
+  if (p->cl) {
+    // the column and row checksums are summed per block: the per-phase
+    // factors N log2 N ride on the energy, tau = gamma u sqrt(weighted energy)
+    p->pass[0].tau_coef = kGamma[dt] * kUnitRoundoff[dt];
+    const int v = cl_variant(ft_mode);
+    bool ok = true;
+    for (const void* fn : {ce->fn_main[0], ce->fn_main[1], ce->fn_fix})
+      ok = ok && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ce->smem[1]) == cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(ce->cluster * 64));
+    cfg.blockDim = dim3((unsigned)ce->nt);
+    cfg.dynamicSmemBytes = (size_t)ce->smem[v];
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)ce->cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    ok = ok && cudaOccupancyMaxActiveClusters(&ncl, ce->fn_main[v], &cfg) == cudaSuccess;
+    if (!ok || ncl < 1) {
+      cudaGetLastError();
+      turbofft_destroy(p);
+      return TURBOFFT_CUDA_ERROR;
+    }
+    p->cl_grid = ncl * ce->cluster;
+  }
+  for (int pi = 0; pi < p->num_passes && !p->cl; ++pi) {
     PassPlan& pp = p->pass[pi];
     pp.ke = reg.find(dt, pp.kind, pp.ns);
     if (!pp.ke) {
@@ -807,7 +970,7 @@ turbofft_status turbofft_plan_create(int64_t n, int64_t batch, turbofft_dtype dt
     for (size_t j = 0; j < hi.size(); ++j) hi[j] = root(n, (int64_t)j * 4096);
     bool ok = (dt == 0) ? (upload<float>(p, &p->d_tlo, lo) && upload<float>(p, &p->d_thi, hi))
                         : (upload<double>(p, &p->d_tlo, lo) && upload<double>(p, &p->d_thi, hi));
-    p->scratch_bytes = (size_t)(batch * n) * elem_bytes(dtype);
+    p->scratch_bytes = p->cl ? 0 : (size_t)(batch * n) * elem_bytes(dtype);
     if (!ok) {
       turbofft_destroy(p);
       return TURBOFFT_ALLOC_FAILED;
@@ -838,8 +1001,60 @@ turbofft_status turbofft_plan_create(int64_t n, int64_t batch, turbofft_dtype dt
     turbofft_destroy(p);
     return TURBOFFT_CUDA_ERROR;
   }
-  if (g_autotune.load() && !t_defer_tune) autotune_with_temp(p);
   *out = p;
+  return TURBOFFT_SUCCESS;
+}
+
+turbofft_status turbofft_plan_create_structured(int64_t n, int64_t batch, turbofft_dtype dtype, int direction,
+                                                turbofft_ft_mode ft_mode, int structure, turbofft_plan** out) {
+  if (out) *out = nullptr;
+  if (structure != TURBOFFT_STRUCTURE_SPLIT && structure != TURBOFFT_STRUCTURE_CLUSTER) return TURBOFFT_INVALID_VALUE;
+  turbofft_status st = create_plan(n, batch, dtype, direction, ft_mode, structure, out);
+  if (st == TURBOFFT_SUCCESS && structure == TURBOFFT_STRUCTURE_CLUSTER && !(*out)->cl) {
+    turbofft_destroy(*out);
+    *out = nullptr;
+    return TURBOFFT_UNSUPPORTED;
+  }
+  if (st == TURBOFFT_SUCCESS && g_autotune.load()) autotune_with_temp(*out);
+  return st;
+}
+
+turbofft_status turbofft_plan_create(int64_t n, int64_t batch, turbofft_dtype dtype, int direction,
+                                     turbofft_ft_mode ft_mode, turbofft_plan** out) {
+  turbofft_status st = create_plan(n, batch, dtype, direction, ft_mode, 0, out);
+  if (st != TURBOFFT_SUCCESS || !g_autotune.load() || t_defer_tune) return st;
+  turbofft_plan* p = *out;
+  autotune_with_temp(p);
+  // where both a cluster plan and a split plan exist for this size, the
+  // faster of the two (after shape tuning) is kept
+  const int dt = dtype == TURBOFFT_C2C_F32 ? 0 : 1;
+  if (registry().find_cl(dt, n)) {
+    const TuneKey key(dt, -1, n, batch, ft_variant(ft_mode), 0);
+    int choice = -1;
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      auto it = g_structure_cache.find(key);
+      if (it != g_structure_cache.end()) choice = it->second;
+    }
+    const int mine = p->cl ? 2 : 1;
+    if (choice != mine) {
+      turbofft_plan* q = nullptr;
+      if (create_plan(n, batch, dtype, direction, ft_mode, mine == 2 ? 1 : 2, &q) == TURBOFFT_SUCCESS) {
+        autotune_with_temp(q);
+        bool take_q = choice == (mine == 2 ? 1 : 2);
+        if (choice < 0) {
+          const double tp = time_with_temp(p), tq = time_with_temp(q);
+          take_q = tq > 0 && (tp <= 0 || tq < tp);
+          std::lock_guard<std::mutex> lock(g_tune_mu);
+          g_structure_cache[key] = take_q ? (mine == 2 ? 1 : 2) : mine;
+        }
+        if (take_q) std::swap(p, q);
+        turbofft_destroy(q);
+      }
+    }
+    p->autotuned = true;
+    *out = p;
+  }
   return TURBOFFT_SUCCESS;
 }
 
@@ -937,7 +1152,7 @@ turbofft_status turbofft_plan_create_ragged(const int64_t* sizes, const int64_t*
     // tune every member on its real (indexed) geometry in shared temporaries
     const size_t bytes = (size_t)extent * elem_bytes(dtype);
     size_t sbytes = 0;
-    for (auto m : p->members) sbytes = std::max(sbytes, m->num_passes == 2 ? m->scratch_bytes : (size_t)0);
+    for (auto m : p->members) sbytes = std::max(sbytes, m->scratch_bytes);
     void *a = nullptr, *b = nullptr, *c = nullptr;
     bool ok = cudaMalloc(&a, bytes) == cudaSuccess && cudaMalloc(&b, bytes) == cudaSuccess &&
               (sbytes == 0 || cudaMalloc(&c, sbytes) == cudaSuccess);
@@ -992,7 +1207,8 @@ turbofft_status turbofft_inject(turbofft_plan* p, turbofft_site site, int bit) {
   if (bit < 0 || bit >= nbits) return TURBOFFT_INVALID_VALUE;
   if (site.transform < 0 || site.transform >= p->batch) return TURBOFFT_INVALID_VALUE;
   if (site.pass < 0 || site.pass >= p->num_passes) return TURBOFFT_INVALID_VALUE;
-  if (site.stage < 0 || site.stage > p->pass[site.pass].ke->stages) return TURBOFFT_INVALID_VALUE;
+  const int nst = p->cl ? (site.pass == 0 ? p->cl->stages_a : p->cl->stages_b) : p->pass[site.pass].ke->stages;
+  if (site.stage < 0 || site.stage > nst) return TURBOFFT_INVALID_VALUE;
   if (site.element < 0 || site.element >= p->n) return TURBOFFT_INVALID_VALUE;
   if (site.component != 0 && site.component != 1) return TURBOFFT_INVALID_VALUE;
   tf::InjectSite s{};
@@ -1030,7 +1246,7 @@ turbofft_status turbofft_exec(turbofft_plan* p, const void* in, void* out, turbo
     cudaError_t e = cudaMemsetAsync(p->d_fts, 0, tf::FT_HEADER_BYTES, s);
     if (e != cudaSuccess) return cuda_fail(p, e, "report reset");
   }
-  if (p->num_passes == 2 && !p->d_scratch) {
+  if (p->scratch_bytes > 0 && !p->d_scratch) {
     if (!dev_alloc(p, &p->d_scratch, p->scratch_bytes)) return TURBOFFT_ALLOC_FAILED;
     p->scratch_owned = true;
   }
@@ -1144,7 +1360,7 @@ turbofft_status turbofft_exec_host(turbofft_plan* p, const void* host_in, void* 
 turbofft_status turbofft_set_workspace(turbofft_plan* p, void* workspace, size_t bytes) {
   if (!p) return TURBOFFT_INVALID_VALUE;
   if (p->ragged) return TURBOFFT_UNSUPPORTED;
-  if (p->num_passes == 1) return TURBOFFT_SUCCESS;  // nothing to place
+  if (p->scratch_bytes == 0) return TURBOFFT_SUCCESS;  // nothing to place
   if (!workspace || bytes < p->scratch_bytes || !aligned16(workspace)) return TURBOFFT_INVALID_VALUE;
   if (p->scratch_owned) {
     cudaStreamSynchronize(nullptr);
@@ -1218,7 +1434,7 @@ turbofft_status turbofft_get_report(turbofft_plan* p, turbofft_report* r) {
 // ---------------------------------------------------------------------------
 namespace tf {
 
-size_t plan_scratch_bytes(const turbofft_plan* p) { return (!p->ragged && p->num_passes == 2) ? p->scratch_bytes : 0; }
+size_t plan_scratch_bytes(const turbofft_plan* p) { return p->ragged ? 0 : p->scratch_bytes; }
 
 int plan_device(const turbofft_plan* p) { return p->device; }
 
@@ -1228,7 +1444,7 @@ turbofft_status exec_given_scratch(turbofft_plan* p, const void* in, void* out, 
   if (!p || !in || !out) return TURBOFFT_INVALID_VALUE;
   if (p->ragged) return TURBOFFT_UNSUPPORTED;
   if (!aligned16(in) || !aligned16(out)) return TURBOFFT_INVALID_VALUE;
-  if (p->num_passes == 2 && (!scratch || !aligned16(scratch))) return TURBOFFT_INVALID_VALUE;
+  if (p->scratch_bytes > 0 && (!scratch || !aligned16(scratch))) return TURBOFFT_INVALID_VALUE;
   const size_t bytes = (size_t)(p->batch * p->n) * elem_bytes(p->dtype);
   const char* a = static_cast<const char*>(in);
   const char* b = static_cast<const char*>(out);

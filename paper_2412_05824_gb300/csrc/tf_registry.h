@@ -26,6 +26,24 @@ struct KernelEntry {
 // all entries of one translation unit
 typedef const KernelEntry* (*EntryTableFn)(int* count);
 
+// single-pass transform of N = n1 * n2 over a cluster of `cluster` blocks
+struct ClEntry {
+  int dtype;
+  int n, n1, n2;
+  int e;            // complex values per thread (both phases)
+  int sa, sb;       // columns (phase A) / rows (phase B) per block
+  int cluster;      // blocks per cluster
+  int nt;           // threads per block
+  int stages_a, stages_b;
+  int smem[2];      // dynamic shared memory: no checksums / checksums
+  LaunchFn main[2];
+  LaunchFn fix;
+  const void* fn_main[2];
+  const void* fn_fix;
+};
+typedef const ClEntry* (*ClTableFn)(int* count);
+const ClEntry* entries_f32_cl(int* count);
+
 const KernelEntry* entries_f32_sp(int* count);
 const KernelEntry* entries_f32_col(int* count);
 const KernelEntry* entries_f32_row(int* count);

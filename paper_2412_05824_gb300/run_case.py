@@ -1,11 +1,11 @@
 """Run one plan configuration a few times on seeded inputs (for profiling a
 single kernel under ncu).
 
-    python -m paper_2412_05824_gb300.run_case DTYPE N FT DIRECTION REPS [LOG2_ELEMENTS]
+    python -m paper_2412_05824_gb300.run_case DTYPE N FT DIRECTION REPS [LOG2_ELEMENTS [STRUCTURE]]
 
 DTYPE float32|float64, FT off|detect|correct|correct_registers,
 DIRECTION forward|inverse|inverse_unscaled; the batch is 2^LOG2_ELEMENTS / N
-(default 2^26 elements).
+(default 2^26 elements); STRUCTURE default|split|cluster.
 """
 import os
 import sys
@@ -23,7 +23,8 @@ def main(argv):
     total = 1 << (int(argv[5]) if len(argv) > 5 else 26)
     x = ss.uniform_complex_torch(1, max(1, total // n), n, dt, device="cuda")
     y = torch.empty_like(x)
-    p = tfl.Plan(n, x.shape[0], x.dtype, d, ft)
+    structure = argv[6] if len(argv) > 6 else "default"
+    p = tfl.Plan(n, x.shape[0], x.dtype, d, ft, structure=structure)
     for _ in range(reps):
         p.exec(x, y)
     torch.cuda.synchronize()
