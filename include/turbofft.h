@@ -172,7 +172,8 @@ turbofft_status turbofft_plan_create(int64_t n, int64_t batch, turbofft_dtype dt
 
 /*
  * Same as turbofft_plan_create with the plan's structure fixed instead of
- * chosen (by default, or by timing when autotuning is on):
+ * chosen (turbofft_plan_create uses SPLIT, or with autotuning on the faster
+ * of the two by timing):
  *   TURBOFFT_STRUCTURE_SPLIT    one kernel pass for n up to the largest
  *                               single-block size (2^13 float32, 2^12
  *                               float64), two four-step passes beyond it
