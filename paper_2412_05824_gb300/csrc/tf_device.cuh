@@ -453,7 +453,8 @@ template <class K> __device__ __forceinline__ long long out_off(const Geo& g, lo
 }
 
 // inter-pass twiddle w_N^{k1 * n2} for column n2 of signal `sig` (KIND_COL):
-// w_N^q = thi[q >> 12] * tlo[q & 4095]
+// w_N^q = thi[q >> 12] * tlo[q & 4095] (two small tables that stay in L1;
+// one table of all N values, read from L2 with no locality, measured slower)
 template <class K> __device__ __forceinline__ typename K::c colTwiddle(const Geo& g, const typename K::c* tlo,
                                                                        const typename K::c* thi, long long sig,
                                                                        int k1) {
@@ -585,8 +586,14 @@ template <class K> constexpr bool paired_ft() {
 }
 template <class K> constexpr int ev_entry_bytes() { return paired_ft<K>() ? 16 : (int)sizeof(typename K::c); }
 template <class K> constexpr bool ev_in_smem() { return 2 * K::NS * ev_entry_bytes<K>() <= 32768; }
+// checksum weight `pos` (table in shared memory for small NS, else global)
+template <class K> __device__ __forceinline__ typename K::c weight(const typename K::c* tab, int pos);
 template <class K, int FTM = 0> constexpr int pass_smem_bytes() {
   return NSTAGE * stage_bytes<K>() + ((FTM != 0 && ev_in_smem<K>()) ? 2 * K::NS * ev_entry_bytes<K>() : 0);
+}
+
+template <class K> __device__ __forceinline__ typename K::c weight(const typename K::c* tab, int pos) {
+  return tab[pos];
 }
 
 // ---------------------------------------------------------------------------
@@ -600,6 +607,20 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N> __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
+
+// Staged tiles of slot-major (SP, ROW) kernels keep each slot's positions
+// XOR-swizzled by (slot % M) * P, in whole 16-byte chunks: when a slot's P
+// threads read fewer than 128 bytes per register index, the M slots of one
+// warp would otherwise read the same banks (M-way conflicts on the first
+// read of every transaction).
+template <class K> struct StageSwz {
+  static constexpr int RUN = K::P * (int)sizeof(typename K::c);  // bytes a slot's threads read per index
+  static constexpr int EPC = 16 / (int)sizeof(typename K::c);    // values per 16-byte chunk
+  static constexpr bool ON = !K::SLOT_FAST && K::P < 32 && RUN < 128 && (K::P % EPC) == 0;
+  static constexpr int M = ON ? 128 / RUN : 1;
+  static __device__ __forceinline__ int x(int slot) { return ON ? (slot % M) * K::P : 0; }
+  static __device__ __forceinline__ int chunk(int slot, int j) { return ON ? (j ^ (x(slot) / EPC)) : j; }
+};
 
 // Issue the copies of work unit `unit`'s input tile into `stage`.  Layout in
 // shared memory: slot-major [slot][pos] for SP/ROW (contiguous in global
@@ -615,18 +636,20 @@ __device__ __forceinline__ void issue_unit(const PassArgs<typename K::real>& A, 
     const long long first = unit * K::S;
     long long nv = g.batch - first;
     if (nv > K::S) nv = K::S;
+    constexpr int cps = K::NS * (int)sizeof(c) / 16;  // 16-byte chunks per transform
+    const int chunks = (int)nv * cps;
     if (g.in_tab == nullptr) {
       const char* src = reinterpret_cast<const char*>(A.in + first * K::NS);
-      const int chunks = (int)(nv * K::NS * (long long)sizeof(c) / 16);
-      for (int q = tid; q < chunks; q += K::NT) cp_async16(stage + 16 * q, src + 16 * (size_t)q);
+      for (int q = tid; q < chunks; q += K::NT) {
+        const int sl = q / cps, j = q - sl * cps;
+        cp_async16(stage + (size_t)sl * K::NS * sizeof(c) + 16 * StageSwz<K>::chunk(sl, j), src + 16 * (size_t)q);
+      }
     } else {
       // indexed transforms: one contiguous run per slot
-      constexpr int cps = K::NS * (int)sizeof(c) / 16;  // 16-byte chunks per transform
-      const int chunks = (int)nv * cps;
       for (int q = tid; q < chunks; q += K::NT) {
         const int sl = q / cps, j = q - sl * cps;
         const char* src = reinterpret_cast<const char*>(A.in + __ldg(g.in_tab + first + sl));
-        cp_async16(stage + (size_t)sl * K::NS * sizeof(c) + 16 * j, src + 16 * (size_t)j);
+        cp_async16(stage + (size_t)sl * K::NS * sizeof(c) + 16 * StageSwz<K>::chunk(sl, j), src + 16 * (size_t)j);
       }
     }
   } else if constexpr (K::KIND == KIND_ROW) {
@@ -634,8 +657,12 @@ __device__ __forceinline__ void issue_unit(const PassArgs<typename K::real>& A, 
     const long long b = unit / blocks;
     const int r0 = (int)(unit - b * blocks) * K::S;
     const char* src = reinterpret_cast<const char*>(A.in + tr_base(g.in_tab, b, g.n) + (long long)r0 * g.n2);
-    constexpr int chunks = K::S * K::NS * (int)sizeof(c) / 16;
-    for (int q = tid; q < chunks; q += K::NT) cp_async16(stage + 16 * q, src + 16 * (size_t)q);
+    constexpr int cps = K::NS * (int)sizeof(c) / 16;
+    constexpr int chunks = K::S * cps;
+    for (int q = tid; q < chunks; q += K::NT) {
+      const int sl = q / cps, j = q - sl * cps;
+      cp_async16(stage + (size_t)sl * K::NS * sizeof(c) + 16 * StageSwz<K>::chunk(sl, j), src + 16 * (size_t)q);
+    }
   } else {
     const int blocks = g.n2 / K::S;
     const long long b = unit / blocks;
@@ -751,7 +778,7 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
     for (int i = 0; i < E; ++i) {
       c v = mk<c>(0, 0);
       const int pos = t + i * P;
-      if (valid) v = K::SLOT_FAST ? sm[pos * S + slot] : sm[slot * K::NS + pos];
+      if (valid) v = K::SLOT_FAST ? sm[pos * S + slot] : sm[slot * K::NS + (pos ^ StageSwz<K>::x(slot))];
       a[i] = conj_mask(v, mask_in);
     }
     __syncthreads();  // the tile is consumed; the stage becomes the exchange buffer
@@ -779,7 +806,7 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
 #pragma unroll
         for (int i = 0; i < E; ++i) {
           if constexpr (EAGER) xs[i] = cadd(xs[i], a[i]);
-          cmac(pin, vvp[t + i * P], a[i]);
+          cmac(pin, weight<K>(vvp, t + i * P), a[i]);
           const float fx = abs_as_float(a[i].x), fy = abs_as_float(a[i].y);
           enf = fmaf(fx, fx, enf);
           enf = fmaf(fy, fy, enf);
@@ -796,11 +823,24 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
         }
       } else {
 #pragma unroll
-        for (int i = 0; i < E; ++i) {
-          if constexpr (EAGER) xs[i] = cadd(xs[i], a[i]);
-          cmac(pin, vvp[t + i * P], a[i]);
-          en = fma(a[i].x, a[i].x, en);
-          en = fma(a[i].y, a[i].y, en);
+        if constexpr (sizeof(R) == 4) {
+          // energy (re^2, im^2) as one paired FP32 FMA per value
+          float2 e2 = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int i = 0; i < E; ++i) {
+            if constexpr (EAGER) xs[i] = cadd(xs[i], a[i]);
+            cmac(pin, weight<K>(vvp, t + i * P), a[i]);
+            e2 = __ffma2_rn(a[i], a[i], e2);
+          }
+          en += e2.x + e2.y;
+        } else {
+#pragma unroll
+          for (int i = 0; i < E; ++i) {
+            if constexpr (EAGER) xs[i] = cadd(xs[i], a[i]);
+            cmac(pin, weight<K>(vvp, t + i * P), a[i]);
+            en = fma(a[i].x, a[i].x, en);
+            en = fma(a[i].y, a[i].y, en);
+          }
         }
       }
     }
@@ -825,10 +865,10 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
           const c w = colTwiddle<K>(g, A.tlo, A.thi, valid ? sig : 0, pos);
           if constexpr (EAGER) ys[i] = cadd(ys[i], a[i]);
           a[i] = cmul(a[i], w);
-          if constexpr (FT) cmac(pout, cmulconj(evp[pos], w), a[i]);
+          if constexpr (FT) cmac(pout, cmulconj(weight<K>(evp, pos), w), a[i]);
         } else {
           if constexpr (EAGER) ys[i] = cadd(ys[i], a[i]);
-          if constexpr (FT) cmac(pout, evp[pos], a[i]);
+          if constexpr (FT) cmac(pout, weight<K>(evp, pos), a[i]);
         }
       }
     } else if constexpr (FT) {
