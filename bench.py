@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ragged", action="store_true", help="skip the ragged-batch comparison")
     ap.add_argument("--no-filter", action="store_true", help="skip the spectral-filter comparison")
+    ap.add_argument("--study", action="store_true",
+                    help="add the ABFT threshold (ROC) and group-size studies (about a minute)")
     return ap.parse_args()
 
 
@@ -591,6 +593,12 @@ def run_ours(args):
 
     ragged = bench_ragged(args, dev, stream, rank, peaks) if not args.no_ragged else None
     sfilter = bench_filter(args, dev, stream) if not args.no_filter else None
+    study = None
+    if args.study and rank == 0:
+        from paper_2412_05824_gb300 import abft_study
+        study = {"roc": [abft_study.roc(1024, 2000, "complex64"), abft_study.roc(1024, 2000, "complex128")],
+                 "group_size": [abft_study.ablation(n, dt) for n, dt in
+                                ((1024, "complex64"), (4096, "complex64"), (1024, "complex128"))]}
 
     launches_per_step = 0
     for dt2, eb2, d2, n2 in cfgs:
@@ -629,6 +637,8 @@ def run_ours(args):
                 "sweep": sweep,
                 "ragged": ragged,
                 "spectral_filter": sfilter}
+        if study is not None:
+            line["abft_study"] = study
         print(json.dumps(line), flush=True)
     for pl in list(plans_ft.values()) + list(plans_plain.values()):
         pl.close()

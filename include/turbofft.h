@@ -297,6 +297,15 @@ turbofft_status turbofft_plan_get_info(const turbofft_plan *plan, turbofft_plan_
 turbofft_status turbofft_set_threshold_scale(turbofft_plan *plan, double factor);
 
 /*
+ * Transactions per checksum group (Sec. 4.3: a thread block verifies its
+ * checksums once per `transactions` transactions; 1 = every transaction, the
+ * thread-block-level scheme without amortisation).  Default 4, range
+ * [1, 16]; for the ablation of the group size (overhead vs. the
+ * single-error-per-group fault model).  Errors: INVALID_VALUE.
+ */
+turbofft_status turbofft_set_group_transactions(turbofft_plan *plan, int transactions);
+
+/*
  * Place the intermediate buffer of a two-pass plan in caller-owned device
  * memory (`bytes` >= info.scratch_bytes, 16-byte aligned) instead of the
  * plan allocating it at its first exec.  Plans that never run at the same

@@ -85,7 +85,7 @@ EXPORTS = [
     "turbofft_destroy", "turbofft_status_string", "turbofft_last_error",
     "turbofft_set_workspace", "turbofft_set_profiling", "turbofft_get_kernel_times",
     "turbofft_exec_static_scratch", "turbofft_plan_create_ragged", "turbofft_plan_get_member_info",
-    "turbofft_set_autotune", "turbofft_plan_create_structured",
+    "turbofft_set_autotune", "turbofft_plan_create_structured", "turbofft_set_group_transactions",
 ]
 
 STATIC_SCRATCH_BYTES = 32 << 20
@@ -110,6 +110,7 @@ def lib() -> ctypes.CDLL:
                                               ctypes.POINTER(vp)]
     L.turbofft_plan_get_member_info.argtypes = [vp, i32, ctypes.POINTER(PlanInfo)]
     L.turbofft_set_autotune.argtypes = [i32]
+    L.turbofft_set_group_transactions.argtypes = [vp, i32]
     L.turbofft_plan_create_structured.argtypes = [i64, i64, i32, i32, i32, i32, ctypes.POINTER(vp)]
     L.turbofft_inject.argtypes = [vp, Site, i32]
     L.turbofft_get_report.argtypes = [vp, ctypes.POINTER(Report)]
@@ -250,6 +251,10 @@ class Plan:
 
     def set_threshold_scale(self, factor: float):
         _check(lib().turbofft_set_threshold_scale(self._h, float(factor)), "turbofft_set_threshold_scale")
+
+    def set_group_transactions(self, transactions: int):
+        """Transactions per checksum group (default 4, range 1..16)."""
+        _check(lib().turbofft_set_group_transactions(self._h, int(transactions)), "turbofft_set_group_transactions")
 
     def close(self):
         if getattr(self, "_h", None):

@@ -1192,6 +1192,14 @@ turbofft_status turbofft_set_threshold_scale(turbofft_plan* p, double factor) {
   return TURBOFFT_SUCCESS;
 }
 
+turbofft_status turbofft_set_group_transactions(turbofft_plan* p, int transactions) {
+  if (!p || transactions < 1 || transactions > 16) return TURBOFFT_INVALID_VALUE;
+  p->T = transactions;
+  for (auto m : p->members) m->T = transactions;
+  if (p->ragged) drop_graph(p);  // the captured launches hold the old group size
+  return TURBOFFT_SUCCESS;
+}
+
 turbofft_status turbofft_inject(turbofft_plan* p, turbofft_site site, int bit) {
   if (!p) return TURBOFFT_INVALID_VALUE;
   if (p->ragged) {
