@@ -242,9 +242,8 @@ __device__ __forceinline__ void cl_body(const ClArgs<typename CL::real>& A, long
     for (int i = 0; i < E; ++i) a[i] = cscale(a[i], A.p.out_scale);
   }
   // ---- transposed store: for each k2 the block's SB rows are contiguous
-  constexpr int SWZ = (1 << KB::B) - 1;
 #pragma unroll
-  for (int i = 0; i < E; ++i) sm[slotB * N2 + ((tB + i * PB) ^ (slotB & SWZ))] = a[i];
+  for (int i = 0; i < E; ++i) sm[slotB * N2 + ((tB + i * PB) ^ tsw<KB>(slotB))] = a[i];
   __syncthreads();
   {
     const int s2 = tid % SB, t2 = tid / SB;
@@ -252,7 +251,7 @@ __device__ __forceinline__ void cl_body(const ClArgs<typename CL::real>& A, long
 #pragma unroll
     for (int i = 0; i < E; ++i) {
       const int k2 = t2 + i * PB;
-      const c v = conj_mask(sm[s2 * N2 + (k2 ^ (s2 & SWZ))], mask_out);
+      const c v = conj_mask(sm[s2 * N2 + (k2 ^ tsw<KB>(s2))], mask_out);
       __stcs(ob + (long long)k2 * N1, v);
     }
   }

@@ -622,6 +622,19 @@ template <class K> struct StageSwz {
   static __device__ __forceinline__ int chunk(int slot, int j) { return ON ? (j ^ (x(slot) / EPC)) : j; }
 };
 
+// XOR swizzle of the row pass's transposed store through shared memory
+// (slot-major buffer, position XOR tsw(slot)).  The read side (32 slots of a
+// warp, one position each) needs slot & (W-1) to differ across W adjacent
+// slots, W = values per 128-byte bank row; the write side (a warp spans
+// 32/P slots, P adjacent positions each) also needs those slots spread over
+// the W/P runs of a bank row when P < W, hence the extra term, which keeps
+// the map a bijection for P >= 2.
+template <class K> __device__ __forceinline__ int tsw(int slot) {
+  constexpr int W = 1 << K::B;
+  constexpr int M = (K::P >= 2 && K::P < W) ? W / K::P : 1;
+  return (slot & (W - 1)) ^ ((slot % M) * K::P);
+}
+
 // Issue the copies of work unit `unit`'s input tile into `stage`.  Layout in
 // shared memory: slot-major [slot][pos] for SP/ROW (contiguous in global
 // memory), position-major [pos][slot] for COL (S adjacent columns of each
@@ -891,7 +904,7 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
       // transposed store: rows r0..r0+S-1 are contiguous in the output for a
       // fixed k2, so go through shared memory and store slot-fast
 #pragma unroll
-      for (int i = 0; i < E; ++i) sm[slot * K::NS + ((t + i * P) ^ (slot & ((1 << K::B) - 1)))] = a[i];
+      for (int i = 0; i < E; ++i) sm[slot * K::NS + ((t + i * P) ^ tsw<K>(slot))] = a[i];
       __syncthreads();
       const int s2 = tid % S, t2 = tid / S;
       const long long sig2 = signal_of<K>(g, unit, s2);
@@ -900,7 +913,7 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         const int pos = t2 + i * P;
-        const c v = conj_mask(sm[s2 * K::NS + (pos ^ (s2 & ((1 << K::B) - 1)))], mask_out);
+        const c v = conj_mask(sm[s2 * K::NS + (pos ^ tsw<K>(s2))], mask_out);
         __stcs(ob + pos * os, v);  // streaming: keep L1 for the tables
       }
       __syncthreads();
