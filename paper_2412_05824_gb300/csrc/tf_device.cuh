@@ -210,7 +210,24 @@ template <class K, int p> struct PassInfo {
 // next pass's contiguous reads free of bank conflicts (Sec. 3.2).
 template <class K, int p> __device__ __forceinline__ int sidx(int slot, int pos) {
   if constexpr (K::SLOT_FAST) {
-    return pos * K::S + slot;
+    // Position-major rows of S values.  When a 128-byte bank row holds
+    // G = W/S > 1 positions, the first pass (twiddle stride 1) writes
+    // positions j*R + m for the 32/S adjacent j of a warp, R/G bank rows
+    // apart, all at the same offset: XOR the position's offset inside its
+    // bank row with bits of j (the row index over max(R/G, 1)), which keeps
+    // the later contiguous reads conflict-free (a permutation inside each
+    // bank row).
+    constexpr int W = 1 << K::B;
+    if constexpr (p == 0 && K::S < W) {
+      constexpr int G = W / K::S;
+      constexpr int LOG_G = ILog2<G>::v;
+      constexpr int R = PassInfo<K, 0>::R;
+      constexpr int SH = (R > G) ? ILog2<R / G>::v : 0;
+      const int key = ((pos >> LOG_G) >> SH) & (G - 1);
+      return (pos ^ key) * K::S + slot;
+    } else {
+      return pos * K::S + slot;
+    }
   } else {
     constexpr int l = PassInfo<K, p>::LOG_L, r = PassInfo<K, p>::LOG_R;
     int q = pos;
