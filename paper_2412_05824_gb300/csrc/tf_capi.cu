@@ -50,7 +50,7 @@ struct Registry {
     }
     tf::EntryTableFn fns[] = {tf::entries_f32_sp, tf::entries_f32_col, tf::entries_f32_row,
                               tf::entries_f64_sp, tf::entries_f64_col, tf::entries_f64_row,
-                              tf::entries_f32_alt_sp, tf::entries_f32_alt_cr};
+                              tf::entries_f32_alt_sp, tf::entries_f32_alt_cr, tf::entries_f64_alt};
     for (auto fn : fns) {
       int n = 0;
       const KernelEntry* t = fn(&n);

@@ -6,7 +6,7 @@ const KernelEntry* entries_f64_sp(int* count) {
       make_entry<Cfg<double, 8, 8, 256, KIND_SP>>(),    make_entry<Cfg<double, 16, 8, 128, KIND_SP>>(),
       make_entry<Cfg<double, 32, 8, 64, KIND_SP>>(),    make_entry<Cfg<double, 64, 8, 32, KIND_SP>>(),
       make_entry<Cfg<double, 128, 8, 16, KIND_SP>>(),   make_entry<Cfg<double, 256, 8, 8, KIND_SP>>(),
-      make_entry<Cfg<double, 512, 8, 4, KIND_SP>>(),    make_entry<Cfg<double, 1024, 8, 2, KIND_SP>>(),
+      make_entry<Cfg<double, 512, 8, 2, KIND_SP>>(),    make_entry<Cfg<double, 1024, 8, 1, KIND_SP>>(),
       make_entry<Cfg<double, 2048, 8, 1, KIND_SP>>(),   make_entry<Cfg<double, 4096, 8, 1, KIND_SP>>(),
 
   };

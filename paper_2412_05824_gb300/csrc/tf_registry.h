@@ -53,5 +53,6 @@ const KernelEntry* entries_f64_row(int* count);
 // alternative shapes (registered after the defaults)
 const KernelEntry* entries_f32_alt_sp(int* count);
 const KernelEntry* entries_f32_alt_cr(int* count);
+const KernelEntry* entries_f64_alt(int* count);
 
 }  // namespace tf
