@@ -96,7 +96,11 @@ typedef struct turbofft_plan turbofft_plan;
  *              at that stage.  For a two-pass plan with n = N1 * N2 the
  *              working array of pass 0 holds column n2 at elements
  *              p * N2 + n2 (p = position within the length-N1 column) and
- *              that of pass 1 holds row k1 at elements k1 * N2 + p.
+ *              that of pass 1 holds row k1 at elements k1 * N2 + p.  A
+ *              three-pass plan (n = N1 * M, M = N2 * N3) has pass 0 as a
+ *              two-pass plan with N2 := M; passes 1 and 2 transform each
+ *              first-pass output row k1 (length M) as a two-pass plan
+ *              N2 x N3 whose working array sits at elements k1 * M + ...
  *   component  0 = real part, 1 = imaginary part
  */
 typedef struct {
@@ -127,16 +131,17 @@ typedef struct {
 typedef struct {
   int64_t n, batch;
   int32_t dtype, direction, ft_mode;
-  int32_t num_passes;       /* 1 or 2 */
-  int64_t sub_n[2];         /* sub-transform length of each pass (n = sub_n[0] * sub_n[1]) */
-  int32_t stages[2];        /* radix stages of each pass */
-  int32_t radix[2];         /* radix of the register-level butterflies of each pass */
+  int32_t num_passes;       /* 1, 2 or 3 */
+  int64_t sub_n[3];         /* sub-transform length of each pass (n = sub_n[0] * sub_n[1] * sub_n[2],
+                               unused entries 1) */
+  int32_t stages[3];        /* radix stages of each pass */
+  int32_t radix[3];         /* radix of the register-level butterflies of each pass */
   int32_t group_transactions; /* transactions of one thread block per checksum group */
-  int32_t grid[2];          /* persistent thread blocks launched per pass */
-  int32_t block[2];         /* threads per block per pass */
+  int32_t grid[3];          /* persistent thread blocks launched per pass */
+  int32_t block[3];         /* threads per block per pass */
   int64_t workspace_bytes;  /* device memory the plan owns or will allocate */
   int64_t scratch_bytes;    /* intermediate buffer of a two-pass plan (0 for one pass) */
-  int32_t per_block[2];     /* transforms (SP) / columns / rows one block holds per transaction */
+  int32_t per_block[3];     /* transforms (SP) / columns / rows one block holds per transaction */
   int32_t num_members;      /* ragged plan: distinct sizes (member plans); 0 otherwise */
   int32_t autotuned;        /* 1 if launch shapes were chosen by timing (turbofft_set_autotune) */
   int32_t cluster;          /* > 0: both passes run in ONE kernel whose thread-block clusters of
@@ -181,11 +186,16 @@ turbofft_status turbofft_plan_create(int64_t n, int64_t batch, turbofft_dtype dt
  *                               share each transform (info.cluster > 0);
  *                               TURBOFFT_UNSUPPORTED for sizes without a
  *                               cluster configuration
+ *   TURBOFFT_STRUCTURE_THREE_PASS  three four-step passes N1 x N2 x N3 (the
+ *                               default for float32 n >= 2^22); for n >= 2^9
+ *                               where every pass has a kernel configuration,
+ *                               else TURBOFFT_UNSUPPORTED
  * Every structure computes the same transform to the same accuracy bar.
  * Errors: as turbofft_plan_create; INVALID_VALUE for another structure.
  */
 #define TURBOFFT_STRUCTURE_SPLIT 1
 #define TURBOFFT_STRUCTURE_CLUSTER 2
+#define TURBOFFT_STRUCTURE_THREE_PASS 3
 turbofft_status turbofft_plan_create_structured(int64_t n, int64_t batch, turbofft_dtype dtype,
                                                 int direction, turbofft_ft_mode ft_mode, int structure,
                                                 turbofft_plan **plan);

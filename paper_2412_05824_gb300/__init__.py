@@ -43,7 +43,8 @@ _DIRS = {"forward": FORWARD, "inverse": INVERSE, "inverse_unscaled": INVERSE_UNS
          INVERSE_UNSCALED: INVERSE_UNSCALED, FORWARD_SCALED: FORWARD_SCALED}
 STRUCTURE_SPLIT = 1
 STRUCTURE_CLUSTER = 2
-_STRUCT = {"split": STRUCTURE_SPLIT, "cluster": STRUCTURE_CLUSTER}
+STRUCTURE_THREE_PASS = 3
+_STRUCT = {"split": STRUCTURE_SPLIT, "cluster": STRUCTURE_CLUSTER, "three_pass": STRUCTURE_THREE_PASS}
 _FT = {"off": FT_OFF, "detect": FT_DETECT, "correct": FT_CORRECT, "correct_registers": FT_CORRECT_REGISTERS,
        None: FT_OFF, False: FT_OFF, FT_OFF: FT_OFF, FT_DETECT: FT_DETECT, FT_CORRECT: FT_CORRECT,
        FT_CORRECT_REGISTERS: FT_CORRECT_REGISTERS}
@@ -66,11 +67,11 @@ class Report(ctypes.Structure):
 class PlanInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("batch", ctypes.c_int64), ("dtype", ctypes.c_int32),
                 ("direction", ctypes.c_int32), ("ft_mode", ctypes.c_int32),
-                ("num_passes", ctypes.c_int32), ("sub_n", ctypes.c_int64 * 2),
-                ("stages", ctypes.c_int32 * 2), ("radix", ctypes.c_int32 * 2),
-                ("group_transactions", ctypes.c_int32), ("grid", ctypes.c_int32 * 2),
-                ("block", ctypes.c_int32 * 2), ("workspace_bytes", ctypes.c_int64),
-                ("scratch_bytes", ctypes.c_int64), ("per_block", ctypes.c_int32 * 2),
+                ("num_passes", ctypes.c_int32), ("sub_n", ctypes.c_int64 * 3),
+                ("stages", ctypes.c_int32 * 3), ("radix", ctypes.c_int32 * 3),
+                ("group_transactions", ctypes.c_int32), ("grid", ctypes.c_int32 * 3),
+                ("block", ctypes.c_int32 * 3), ("workspace_bytes", ctypes.c_int64),
+                ("scratch_bytes", ctypes.c_int64), ("per_block", ctypes.c_int32 * 3),
                 ("num_members", ctypes.c_int32), ("autotuned", ctypes.c_int32),
                 ("cluster", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
@@ -159,8 +160,8 @@ class Plan:
     def __init__(self, n: int, batch: int, dtype="complex64", direction="forward", ft="off",
                  structure="default"):
         """structure: "default" (chosen by the library), "split" (one pass or
-        two four-step passes) or "cluster" (one pass over thread-block
-        clusters)."""
+        two four-step passes), "cluster" (one pass over thread-block
+        clusters) or "three_pass"."""
         self.n, self.batch = int(n), int(batch)
         self.dtype_code = _dtype_code(dtype)
         self.direction = _DIRS[direction]

@@ -160,6 +160,9 @@ int ilog2_exact(int64_t n) {
 // default threshold factor gamma per working precision: chosen from clean-run
 // residuals so that the largest clean |S1| stays far below tau
 const double kGamma[2] = {8.0, 16.0};
+
+// float32 sizes from 2^this use three passes by default
+const int kThreePassLog2F32 = 22;
 const double kUnitRoundoff[2] = {0x1p-24, 0x1p-53};
 
 int g_num_sms = 0;
@@ -174,7 +177,15 @@ struct PassPlan {
   int kind = 0;
   int ns = 0;
   int grid = 0;
-  long long units_per_batch_item = 0;  // work units per transform (COL/ROW), SP: see units()
+  // geometry the pass works on: sub-transforms of length g_n = g_n1 * g_n2,
+  // bm of them per transform of the plan (three-pass plans: N1 for the
+  // second and third passes); outer = N1 for the third pass's output mapping
+  long long g_n = 0;
+  int g_n1 = 0, g_n2 = 1;
+  long long bm = 1;
+  int outer = 0;
+  void* d_tlo = nullptr;  // inter-pass twiddles of a column pass over length g_n
+  void* d_thi = nullptr;
   void* d_tw = nullptr;
   void* d_ev = nullptr;
   void* d_vv = nullptr;
@@ -189,7 +200,7 @@ struct turbofft_plan {
   int device = 0;
   int num_passes = 1;
   int n1 = 0, n2 = 1;
-  PassPlan pass[2];
+  PassPlan pass[3];
   void* d_tlo = nullptr;
   void* d_thi = nullptr;
   void* d_scratch = nullptr;      // intermediate of two-pass plans (owned or caller's)
@@ -315,8 +326,15 @@ bool set_smem_attrs(const KernelEntry* ke) {
 long long units_for(const turbofft_plan* p, int pi, int64_t batch) {
   const PassPlan& pp = p->pass[pi];
   if (pp.kind == tf::KIND_SP) return (batch + pp.ke->s - 1) / pp.ke->s;
-  if (pp.kind == tf::KIND_COL) return batch * (p->n2 / pp.ke->s);
-  return batch * (p->n1 / pp.ke->s);
+  if (pp.kind == tf::KIND_COL) return batch * pp.bm * (pp.g_n2 / pp.ke->s);
+  return batch * pp.bm * (pp.g_n1 / pp.ke->s);
+}
+
+// sub-transforms ("signals") of pass pi per transform of the plan
+int64_t signals_per_transform(const turbofft_plan* p, int pi) {
+  const PassPlan& pp = p->pass[pi];
+  if (pp.kind == tf::KIND_SP) return 1;
+  return pp.bm * (pp.kind == tf::KIND_COL ? pp.g_n2 : pp.g_n1);
 }
 
 template <typename R>
@@ -332,14 +350,16 @@ void fill_args(const turbofft_plan* p, int pi, const void* in, void* out, int64_
   A.vv = static_cast<const c*>(pp.d_vv);
   A.ev4 = static_cast<const float4*>(pp.d_ev4);
   A.vv4 = static_cast<const float4*>(pp.d_vv4);
-  A.tlo = static_cast<const c*>(p->d_tlo);
-  A.thi = static_cast<const c*>(p->d_thi);
-  A.geo.n = p->n;
-  A.geo.n1 = p->n1;
-  A.geo.n2 = p->n2;
-  A.geo.batch = batch;
+  A.tlo = static_cast<const c*>(pp.d_tlo ? pp.d_tlo : p->d_tlo);
+  A.thi = static_cast<const c*>(pp.d_thi ? pp.d_thi : p->d_thi);
+  A.geo.n = pp.g_n;
+  A.geo.n1 = pp.g_n1;
+  A.geo.n2 = pp.g_n2;
+  A.geo.batch = batch * pp.bm;
   A.geo.in_tab = (pi == 0) ? p->d_tab : nullptr;
   A.geo.out_tab = (pi == p->num_passes - 1) ? p->d_tab : nullptr;
+  A.geo.outer = pp.outer;
+  A.geo.n_outer = p->n;
   A.num_units = p->cl ? batch : units_for(p, pi, batch);  // cluster plans: one unit per transform
   const bool inverse = p->direction > 0;
   const bool scaled = p->direction == TURBOFFT_INVERSE || p->direction == TURBOFFT_FORWARD_SCALED;
@@ -410,8 +430,9 @@ turbofft_status run(turbofft_plan* p, const void* in, void* out, void* scratch, 
   }
   for (int pi = 0; pi < p->num_passes; ++pi) {
     const PassPlan& pp = p->pass[pi];
-    const void* pin = (pi == 0) ? in : scratch;
-    void* pout = (pi == p->num_passes - 1) ? out : scratch;
+    // two passes: in -> scratch -> out; three: in -> out -> scratch -> out
+    const void* pin = (pi == 0) ? in : (p->num_passes == 3 && pi == 1 ? out : scratch);
+    void* pout = (pi == p->num_passes - 1 || (p->num_passes == 3 && pi == 0)) ? out : scratch;
     long long units = units_for(p, pi, batch);
     int grid = (int)std::min<long long>(units, pp.grid);
     if (grid < 1) grid = 1;
@@ -506,7 +527,9 @@ turbofft_status queue_plan(turbofft_plan* p, const void* in, void* out, void* sc
 // geometry and the fastest kept.  Results are cached per process.
 // ---------------------------------------------------------------------------
 std::atomic<int> g_autotune{0};
-thread_local bool t_defer_tune = false;  // ragged members are tuned after their offsets are set
+// set while the members of a ragged plan are created: they are tuned after
+// their offset tables exist, and keep to one or two passes
+thread_local bool t_ragged_member = false;
 std::mutex g_tune_mu;
 typedef std::tuple<int, int, int64_t, int64_t, int, int> TuneKey;  // dtype, pass, n, batch, variant, indexed
 std::map<TuneKey, const KernelEntry*> g_tune_cache;
@@ -745,10 +768,8 @@ void add_report(const turbofft_plan* m, const std::vector<int64_t>* ids, turboff
       r->first_threshold = rc.tau;
     }
     if (rc.signal >= 0 && r->first_transform < 0) {
-      const int kind = m->pass[rc.pass_id].kind;
-      int64_t tr = rc.signal;  // cluster plans record the transform itself
-      if (!m->cl && kind == tf::KIND_COL) tr = rc.signal / m->n2;
-      if (!m->cl && kind == tf::KIND_ROW) tr = rc.signal / m->n1;
+      // cluster plans record the transform itself
+      int64_t tr = m->cl ? rc.signal : rc.signal / signals_per_transform(m, rc.pass_id);
       tr += rc.transform_base;
       r->first_transform = (ids && tr >= 0 && tr < (int64_t)ids->size()) ? (*ids)[tr] : tr;
     }
@@ -784,6 +805,7 @@ void fill_info(const turbofft_plan* p, turbofft_plan_info* info) {
       info->block[pi] = ce->nt;
       info->per_block[pi] = pi == 0 ? ce->sa : ce->sb;
     }
+    info->sub_n[2] = 1;
     info->workspace_bytes = p->workspace_bytes;
     info->scratch_bytes = 0;
     return;
@@ -796,7 +818,7 @@ void fill_info(const turbofft_plan* p, turbofft_plan_info* info) {
     info->block[pi] = p->pass[pi].ke->nt;
     info->per_block[pi] = p->pass[pi].ke->s;
   }
-  if (p->num_passes == 1) info->sub_n[1] = 1;
+  for (int pi = p->num_passes; pi < 3; ++pi) info->sub_n[pi] = 1;
   info->workspace_bytes = p->workspace_bytes + (p->scratch_owned ? 0 : (int64_t)p->scratch_bytes);
   info->scratch_bytes = (int64_t)p->scratch_bytes;
 }
@@ -883,8 +905,15 @@ static turbofft_status create_plan(int64_t n, int64_t batch, turbofft_dtype dtyp
   const int dt = dtype == TURBOFFT_C2C_F32 ? 0 : 1;
 
   // pass split: one pass up to the largest single-pass size, else N1 x N2
-  // passes; the cluster single pass when asked for (or chosen by timing)
+  // passes, or N1 x N2 x N3 for large float32 sizes (three passes whose
+  // column tiles stay 64-128 bytes wide); the cluster single pass when
+  // asked for (or chosen by timing)
   const ClEntry* ce = reg.find_cl(dt, n);
+  const bool three = structure == 3 || (structure == 0 && dt == 0 && logn >= kThreePassLog2F32 && !t_ragged_member);
+  if (structure == 3 && (logn < 9 || t_ragged_member)) {
+    delete p;
+    return TURBOFFT_UNSUPPORTED;
+  }
   if (ce && structure == 2) {
     p->cl = ce;
     p->num_passes = 2;
@@ -894,6 +923,17 @@ static turbofft_status create_plan(int64_t n, int64_t batch, turbofft_dtype dtyp
     p->pass[0].ns = ce->n1;
     p->pass[1].kind = tf::KIND_ROW;
     p->pass[1].ns = ce->n2;
+  } else if (three) {
+    const int a = logn / 3, b = (logn - a) / 2, c = logn - a - b;
+    p->num_passes = 3;
+    p->n1 = 1 << a;
+    p->n2 = 1 << (b + c);
+    p->pass[0].kind = tf::KIND_COL;
+    p->pass[0].ns = 1 << a;
+    p->pass[1].kind = tf::KIND_COL;
+    p->pass[1].ns = 1 << b;
+    p->pass[2].kind = tf::KIND_ROW;
+    p->pass[2].ns = 1 << c;
   } else if (n <= reg.max_sp(dt)) {
     p->num_passes = 1;
     p->n1 = (int)n;
@@ -908,6 +948,21 @@ static turbofft_status create_plan(int64_t n, int64_t batch, turbofft_dtype dtyp
     p->pass[0].ns = p->n1;
     p->pass[1].kind = tf::KIND_ROW;
     p->pass[1].ns = p->n2;
+  }
+  // geometry of each pass
+  for (int pi = 0; pi < p->num_passes; ++pi) {
+    PassPlan& pp = p->pass[pi];
+    pp.g_n = n;
+    pp.g_n1 = p->n1;
+    pp.g_n2 = p->n2;
+    pp.bm = 1;
+    if (p->num_passes == 3 && pi > 0) {
+      pp.g_n = p->n2;  // M = N2 * N3, one length-M transform per first-pass output row
+      pp.g_n1 = p->pass[1].ns;
+      pp.g_n2 = p->pass[2].ns;
+      pp.bm = p->n1;
+      pp.outer = (pi == 2) ? p->n1 : 0;
+    }
   }
   for (int pi = 0; pi < p->num_passes && p->cl; ++pi) {
     if (!upload_tables(p, p->pass[pi])) {
@@ -947,12 +1002,12 @@ static turbofft_status create_plan(int64_t n, int64_t batch, turbofft_dtype dtyp
     PassPlan& pp = p->pass[pi];
     pp.ke = reg.find(dt, pp.kind, pp.ns);
     if (!pp.ke) {
-      delete p;
+      turbofft_destroy(p);
       return TURBOFFT_UNSUPPORTED;
     }
     if (!set_smem_attrs(pp.ke)) {
       cudaGetLastError();
-      delete p;
+      turbofft_destroy(p);
       return TURBOFFT_CUDA_ERROR;
     }
     const int occ = occupancy_blocks(pp.ke, ft_variant(ft_mode));
@@ -963,13 +1018,21 @@ static turbofft_status create_plan(int64_t n, int64_t batch, turbofft_dtype dtyp
       return TURBOFFT_ALLOC_FAILED;
     }
   }
-  if (p->num_passes == 2) {
-    // inter-pass twiddles w_N^q = thi[q >> 12] * tlo[q & 4095]
-    std::vector<cld> lo(4096), hi((size_t)std::max<int64_t>(1, n / 4096));
-    for (int j = 0; j < 4096; ++j) lo[j] = root(n, j);
-    for (size_t j = 0; j < hi.size(); ++j) hi[j] = root(n, (int64_t)j * 4096);
-    bool ok = (dt == 0) ? (upload<float>(p, &p->d_tlo, lo) && upload<float>(p, &p->d_thi, hi))
-                        : (upload<double>(p, &p->d_tlo, lo) && upload<double>(p, &p->d_thi, hi));
+  if (p->num_passes >= 2) {
+    // inter-pass twiddles w_L^q = thi[q >> 12] * tlo[q & 4095] of each
+    // column pass, over the length L it splits (N, and M for the second
+    // pass of a three-pass plan)
+    bool ok = true;
+    for (int pi = 0; pi + 1 < p->num_passes && ok; ++pi) {
+      const int64_t L = p->pass[pi].g_n;
+      void** lo_dst = (pi == 0) ? &p->d_tlo : &p->pass[pi].d_tlo;
+      void** hi_dst = (pi == 0) ? &p->d_thi : &p->pass[pi].d_thi;
+      std::vector<cld> lo(4096), hi((size_t)std::max<int64_t>(1, L / 4096));
+      for (int j = 0; j < 4096; ++j) lo[j] = root(L, j);
+      for (size_t j = 0; j < hi.size(); ++j) hi[j] = root(L, (int64_t)j * 4096);
+      ok = (dt == 0) ? (upload<float>(p, lo_dst, lo) && upload<float>(p, hi_dst, hi))
+                     : (upload<double>(p, lo_dst, lo) && upload<double>(p, hi_dst, hi));
+    }
     p->scratch_bytes = p->cl ? 0 : (size_t)(batch * n) * elem_bytes(dtype);
     if (!ok) {
       turbofft_destroy(p);
@@ -990,7 +1053,8 @@ static turbofft_status create_plan(int64_t n, int64_t batch, turbofft_dtype dtyp
       return TURBOFFT_ALLOC_FAILED;
     }
     memset(p->h_fts, 0, sizeof(FtState));
-    p->rec_stride = std::max(p->pass[0].ns, p->num_passes == 2 ? p->pass[1].ns : 0);
+    p->rec_stride = 0;
+    for (int pi = 0; pi < p->num_passes; ++pi) p->rec_stride = std::max(p->rec_stride, p->pass[pi].ns);
     if (!dev_alloc(p, &p->d_rec_sums, (size_t)tf::MAX_RECORDS * 2 * p->rec_stride * elem_bytes(dtype))) {
       turbofft_destroy(p);
       return TURBOFFT_ALLOC_FAILED;
@@ -1008,7 +1072,9 @@ static turbofft_status create_plan(int64_t n, int64_t batch, turbofft_dtype dtyp
 turbofft_status turbofft_plan_create_structured(int64_t n, int64_t batch, turbofft_dtype dtype, int direction,
                                                 turbofft_ft_mode ft_mode, int structure, turbofft_plan** out) {
   if (out) *out = nullptr;
-  if (structure != TURBOFFT_STRUCTURE_SPLIT && structure != TURBOFFT_STRUCTURE_CLUSTER) return TURBOFFT_INVALID_VALUE;
+  if (structure != TURBOFFT_STRUCTURE_SPLIT && structure != TURBOFFT_STRUCTURE_CLUSTER &&
+      structure != TURBOFFT_STRUCTURE_THREE_PASS)
+    return TURBOFFT_INVALID_VALUE;
   turbofft_status st = create_plan(n, batch, dtype, direction, ft_mode, structure, out);
   if (st == TURBOFFT_SUCCESS && structure == TURBOFFT_STRUCTURE_CLUSTER && !(*out)->cl) {
     turbofft_destroy(*out);
@@ -1022,7 +1088,7 @@ turbofft_status turbofft_plan_create_structured(int64_t n, int64_t batch, turbof
 turbofft_status turbofft_plan_create(int64_t n, int64_t batch, turbofft_dtype dtype, int direction,
                                      turbofft_ft_mode ft_mode, turbofft_plan** out) {
   turbofft_status st = create_plan(n, batch, dtype, direction, ft_mode, 0, out);
-  if (st != TURBOFFT_SUCCESS || !g_autotune.load() || t_defer_tune) return st;
+  if (st != TURBOFFT_SUCCESS || !g_autotune.load() || t_ragged_member) return st;
   turbofft_plan* p = *out;
   autotune_with_temp(p);
   // where both a cluster plan and a split plan exist for this size, the
@@ -1105,7 +1171,7 @@ turbofft_status turbofft_plan_create_ragged(const int64_t* sizes, const int64_t*
   }
   p->member_of.assign((size_t)count, 0);
   p->local_of.assign((size_t)count, 0);
-  t_defer_tune = true;
+  t_ragged_member = true;
   turbofft_status st = TURBOFFT_SUCCESS;
   for (auto& g : groups) {
     turbofft_plan* m = nullptr;
@@ -1128,7 +1194,7 @@ turbofft_status turbofft_plan_create_ragged(const int64_t* sizes, const int64_t*
     }
     m->d_tab = static_cast<long long*>(d);
   }
-  t_defer_tune = false;
+  t_ragged_member = false;
   if (st != TURBOFFT_SUCCESS) {
     turbofft_destroy(p);
     return st;
@@ -1225,16 +1291,21 @@ turbofft_status turbofft_inject(turbofft_plan* p, turbofft_site site, int bit) {
   s.stage = site.stage;
   s.comp = site.component;
   s.bit = bit;
-  const int kind = p->pass[site.pass].kind;
-  if (kind == tf::KIND_SP) {
+  const PassPlan& ip = p->pass[site.pass];
+  if (ip.kind == tf::KIND_SP) {
     s.signal = site.transform;
     s.pos = (int)site.element;
-  } else if (kind == tf::KIND_COL) {
-    s.signal = site.transform * p->n2 + site.element % p->n2;
-    s.pos = (int)(site.element / p->n2);
   } else {
-    s.signal = site.transform * p->n1 + site.element / p->n2;
-    s.pos = (int)(site.element % p->n2);
+    // element = sub * g_n + el: sub-transform `sub` of the pass's bm per transform
+    const int64_t sub = site.element / ip.g_n, el = site.element % ip.g_n;
+    const int64_t r = site.transform * ip.bm + sub;
+    if (ip.kind == tf::KIND_COL) {
+      s.signal = r * ip.g_n2 + el % ip.g_n2;
+      s.pos = (int)(el / ip.g_n2);
+    } else {
+      s.signal = r * ip.g_n1 + el / ip.g_n2;
+      s.pos = (int)(el % ip.g_n2);
+    }
   }
   p->armed = s;
   return TURBOFFT_SUCCESS;
@@ -1337,8 +1408,7 @@ turbofft_status turbofft_exec_host(turbofft_plan* p, const void* host_in, void* 
     tf::InjectSite cinj = inj;
     if (inj.active) {
       // the armed transform belongs to exactly one chunk
-      const int kind = p->pass[inj.pass].kind;
-      const int64_t per_tr = (kind == tf::KIND_SP) ? 1 : (kind == tf::KIND_COL ? p->n2 : p->n1);
+      const int64_t per_tr = signals_per_transform(p, inj.pass);
       const int64_t tr = inj.signal / per_tr;
       if (tr >= b0 && tr < b0 + nb) cinj.signal = inj.signal - b0 * per_tr;
       else cinj.active = 0;

@@ -405,10 +405,25 @@ struct Geo {
   // the contiguous layout b * N (ragged batches index their transforms)
   const long long* in_tab;
   const long long* out_tab;
+  // last pass of a three-pass plan (outer > 1): this pass's transforms are
+  // the rows b = t * outer + k1 of transform t of length n_outer, and element
+  // k' of row b goes to k1 + outer * k' of transform t (0 or 1: no mapping)
+  int outer;
+  long long n_outer;
 };
 
 __device__ __forceinline__ long long tr_base(const long long* tab, long long b, long long n) {
   return tab ? __ldg(tab + b) : b * n;
+}
+
+// three-pass last pass: first sub-transform of unit `unit` (units walk
+// transform t, then row k2, then blocks of S adjacent sub-transforms)
+template <class K> __device__ __forceinline__ long long row_unit_first(const Geo& g, long long unit) {
+  const int kblocks = g.outer / K::S;
+  const long long per_t = (long long)g.n1 * kblocks;
+  const long long t = unit / per_t;
+  const int kb = (int)((unit - t * per_t) % kblocks);
+  return t * g.outer + (long long)kb * K::S;
 }
 
 // signal id of slot `slot` of work unit `unit`; -1 if past the end (ragged tail)
@@ -422,6 +437,15 @@ template <class K> __device__ __forceinline__ long long signal_of(const Geo& g, 
     int n2 = (int)(unit - b * blocks) * K::S + slot;
     return b * g.n2 + n2;
   } else {
+    if (g.outer > 1) {
+      // last pass of a three-pass plan: the S rows of a unit are row k2 of
+      // S adjacent sub-transforms (adjacent first-pass outputs k1), whose
+      // results are adjacent in the final output
+      const long long b0 = row_unit_first<K>(g, unit);
+      const long long per_t = (long long)g.n1 * (g.outer / K::S);
+      const int k2 = (int)((unit % per_t) / (g.outer / K::S));
+      return (b0 + slot) * g.n1 + k2;
+    }
     const int blocks = g.n1 / K::S;
     long long b = unit / blocks;
     int k1 = (int)(unit - b * blocks) * K::S + slot;
@@ -456,11 +480,16 @@ template <class K> __device__ __forceinline__ long long out_base(const Geo& g, l
     return tr_base(g.out_tab, b, g.n) + (sig - b * g.n2);
   } else {
     const long long b = sig / g.n1;
+    if (g.outer > 1) {
+      const long long tb = b / g.outer;
+      return tr_base(g.out_tab, tb, g.n_outer) + (b - tb * g.outer) + (sig - b * g.n1) * g.outer;
+    }
     return tr_base(g.out_tab, b, g.n) + (sig - b * g.n1);
   }
 }
 template <class K> __device__ __forceinline__ long long out_step(const Geo& g) {
-  return K::KIND == KIND_SP ? 1 : (K::KIND == KIND_COL ? (long long)g.n2 : (long long)g.n1);
+  if constexpr (K::KIND == KIND_ROW) return (long long)g.n1 * (g.outer > 1 ? g.outer : 1);
+  return K::KIND == KIND_SP ? 1 : (long long)g.n2;
 }
 template <class K> __device__ __forceinline__ long long in_off(const Geo& g, long long sig, int pos) {
   return in_base<K>(g, sig) + (long long)pos * in_step<K>(g);
@@ -683,6 +712,20 @@ __device__ __forceinline__ void issue_unit(const PassArgs<typename K::real>& A, 
       }
     }
   } else if constexpr (K::KIND == KIND_ROW) {
+    if (g.outer > 1) {
+      // rows of S different sub-transforms: one contiguous run per slot
+      constexpr int cps = K::NS * (int)sizeof(c) / 16;
+      const long long b0 = row_unit_first<K>(g, unit);
+      const long long per_t = (long long)g.n1 * (g.outer / K::S);
+      const int k2 = (int)((unit % per_t) / (g.outer / K::S));
+      const c* base = A.in + b0 * g.n + (long long)k2 * g.n2;
+      for (int q = tid; q < K::S * cps; q += K::NT) {
+        const int sl = q / cps, j = q - sl * cps;
+        cp_async16(stage + (size_t)sl * K::NS * sizeof(c) + 16 * StageSwz<K>::chunk(sl, j),
+                   reinterpret_cast<const char*>(base + (long long)sl * g.n) + 16 * j);
+      }
+      return;
+    }
     const int blocks = g.n1 / K::S;
     const long long b = unit / blocks;
     const int r0 = (int)(unit - b * blocks) * K::S;
