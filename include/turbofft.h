@@ -8,7 +8,9 @@
  *       inverse  x_j = (1/N) sum_n y_n exp(+2 pi i j n / N)
  *     computed as a Stockham FFT (Sec. 3.2), in one pass over HBM for
  *     N <= 2^13 (float32) / 2^12 (float64) and in two passes (four-step,
- *     N = N1 * N2, the kernel-level tiling of Sec. 3.1) up to N = 2^24.
+ *     N = N1 * N2, the kernel-level tiling of Sec. 3.1) up to N = 2^24
+ *     (three passes N1 * N2 * N3 for float32 N >= 2^22; optionally one pass
+ *     over a thread-block cluster for float32 2^13..2^16).
  *   - Fault tolerance: the two-sided checksum of Sec. 4.1 (Eq. 4-5) fused
  *     into the transform kernels (Sec. 4.2.2), amortised over several
  *     transactions of one thread block (Sec. 4.3), with the location
