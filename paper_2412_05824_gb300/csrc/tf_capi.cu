@@ -284,6 +284,9 @@ bool upload_tables(turbofft_plan* p, PassPlan& pp) {
   std::vector<cld> v = e;
   host_fft(v);  // v = W e = (e^T W)^T, W symmetric (Eq. 1)
   if (p->dtype == TURBOFFT_C2C_F32) {
+    bool ok = upload<float>(p, &pp.d_tw, tw) && upload<float>(p, &pp.d_ev, e) && upload<float>(p, &pp.d_vv, v);
+#ifdef TF_PAIRED_CHECKSUMS
+    // weights arranged as (re, re, im, im) for the paired-FMA checksum build
     auto arranged = [&](void** dst, const std::vector<cld>& src) {
       std::vector<float4> t4(src.size());
       for (size_t i = 0; i < src.size(); ++i) {
@@ -293,8 +296,9 @@ bool upload_tables(turbofft_plan* p, PassPlan& pp) {
       const size_t bytes = t4.size() * sizeof(float4);
       return dev_alloc(p, dst, bytes) && cudaMemcpy(*dst, t4.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess;
     };
-    return upload<float>(p, &pp.d_tw, tw) && upload<float>(p, &pp.d_ev, e) && upload<float>(p, &pp.d_vv, v) &&
-           arranged(&pp.d_ev4, e) && arranged(&pp.d_vv4, v);
+    ok = ok && arranged(&pp.d_ev4, e) && arranged(&pp.d_vv4, v);
+#endif
+    return ok;
   }
   return upload<double>(p, &pp.d_tw, tw) && upload<double>(p, &pp.d_ev, e) && upload<double>(p, &pp.d_vv, v);
 }
