@@ -405,18 +405,19 @@ int cl_variant(int ft_mode) { return ft_mode == TURBOFFT_FT_OFF ? 0 : 1; }
 turbofft_status run(turbofft_plan* p, const void* in, void* out, void* scratch, int64_t batch, int64_t tbase,
                     cudaStream_t stream, const tf::InjectSite& inj) {
   const bool ft = p->ft_mode != TURBOFFT_FT_OFF;
+  // CUDA events around each kernel when profiling (kind = 2 * pass + is_correction)
+  auto timed = [&](int kind, auto&& launch) {
+    const bool prof = p->profiling && p->nprof < 8;
+    if (prof) cudaEventRecord(p->prof_ev[p->nprof][0], stream);
+    launch();
+    if (prof) {
+      cudaEventRecord(p->prof_ev[p->nprof][1], stream);
+      p->prof_kind[p->nprof++] = kind;
+    }
+  };
   if (p->cl) {
     const ClEntry* ce = p->cl;
     const int grid = (int)std::min<long long>((long long)p->cl_grid, (long long)batch * ce->cluster);
-    auto timed = [&](int kind, auto&& launch) {
-      const bool prof = p->profiling && p->nprof < 8;
-      if (prof) cudaEventRecord(p->prof_ev[p->nprof][0], stream);
-      launch();
-      if (prof) {
-        cudaEventRecord(p->prof_ev[p->nprof][1], stream);
-        p->prof_kind[p->nprof++] = kind;
-      }
-    };
     if (p->dtype == TURBOFFT_C2C_F32) {
       tf::ClArgs<float> A;
       fill_cl_args<float>(p, in, out, batch, tbase, inj, A);
@@ -440,15 +441,6 @@ turbofft_status run(turbofft_plan* p, const void* in, void* out, void* scratch, 
     long long units = units_for(p, pi, batch);
     int grid = (int)std::min<long long>(units, pp.grid);
     if (grid < 1) grid = 1;
-    auto timed = [&](int kind, auto&& launch) {
-      const bool prof = p->profiling && p->nprof < 8;
-      if (prof) cudaEventRecord(p->prof_ev[p->nprof][0], stream);
-      launch();
-      if (prof) {
-        cudaEventRecord(p->prof_ev[p->nprof][1], stream);
-        p->prof_kind[p->nprof++] = kind;
-      }
-    };
     if (p->dtype == TURBOFFT_C2C_F32) {
       tf::PassArgs<float> A;
       fill_args<float>(p, pi, pin, pout, batch, tbase, inj, A);
@@ -522,6 +514,31 @@ turbofft_status queue_plan(turbofft_plan* p, const void* in, void* out, void* sc
     cudaError_t e = cudaMemcpyAsync(p->h_fts, p->d_fts, sizeof(FtState), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_fail(p, e, "report copy");
   }
+  return TURBOFFT_SUCCESS;
+}
+
+// the buffers a (non-ragged) exec may use: 16-byte aligned, not overlapping
+turbofft_status check_io(const turbofft_plan* p, const void* in, void* out) {
+  if (!in || !out) return TURBOFFT_INVALID_VALUE;
+  if (!aligned16(in) || !aligned16(out)) return TURBOFFT_INVALID_VALUE;
+  const size_t bytes = (size_t)(p->ragged ? p->extent : p->batch * p->n) * elem_bytes(p->dtype);
+  const char* a = static_cast<const char*>(in);
+  const char* b = static_cast<const char*>(out);
+  if (a < b + bytes && b < a + bytes) return TURBOFFT_UNSUPPORTED;
+  return TURBOFFT_SUCCESS;
+}
+
+// one exec of a plan on `s` with the armed site (then disarmed); the plan's
+// `done` event marks its end for turbofft_get_report
+turbofft_status exec_on_stream(turbofft_plan* p, const void* in, void* out, void* scratch, cudaStream_t s) {
+  const tf::InjectSite inj = p->armed;
+  p->armed.active = 0;
+  p->nprof = 0;
+  turbofft_status st = queue_plan(p, in, out, scratch, s, inj);
+  if (st != TURBOFFT_SUCCESS) return st;
+  cudaError_t e = cudaEventRecord(p->done, s);
+  if (e != cudaSuccess) return cuda_fail(p, e, "event record");
+  p->have_exec = true;
   return TURBOFFT_SUCCESS;
 }
 
@@ -1316,36 +1333,16 @@ turbofft_status turbofft_inject(turbofft_plan* p, turbofft_site site, int bit) {
 }
 
 turbofft_status turbofft_exec(turbofft_plan* p, const void* in, void* out, turbofft_stream stream) {
-  if (!p || !in || !out) return TURBOFFT_INVALID_VALUE;
-  if (!aligned16(in) || !aligned16(out)) return TURBOFFT_INVALID_VALUE;
-  const size_t bytes = (size_t)(p->ragged ? p->extent : p->batch * p->n) * elem_bytes(p->dtype);
-  const char* a = static_cast<const char*>(in);
-  const char* b = static_cast<const char*>(out);
-  if (a < b + bytes && b < a + bytes) return TURBOFFT_UNSUPPORTED;
+  if (!p) return TURBOFFT_INVALID_VALUE;
+  turbofft_status st = check_io(p, in, out);
+  if (st != TURBOFFT_SUCCESS) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (p->ragged) return exec_ragged(p, in, out, s);
-  const bool ft = p->ft_mode != TURBOFFT_FT_OFF;
-  if (ft) {
-    cudaError_t e = cudaMemsetAsync(p->d_fts, 0, tf::FT_HEADER_BYTES, s);
-    if (e != cudaSuccess) return cuda_fail(p, e, "report reset");
-  }
   if (p->scratch_bytes > 0 && !p->d_scratch) {
     if (!dev_alloc(p, &p->d_scratch, p->scratch_bytes)) return TURBOFFT_ALLOC_FAILED;
     p->scratch_owned = true;
   }
-  tf::InjectSite inj = p->armed;
-  p->armed.active = 0;
-  p->nprof = 0;
-  turbofft_status st = run(p, in, out, p->d_scratch, p->batch, 0, s, inj);
-  if (st != TURBOFFT_SUCCESS) return st;
-  if (ft) {
-    cudaError_t e = cudaMemcpyAsync(p->h_fts, p->d_fts, sizeof(FtState), cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return cuda_fail(p, e, "report copy");
-  }
-  cudaError_t e = cudaEventRecord(p->done, s);
-  if (e != cudaSuccess) return cuda_fail(p, e, "event record");
-  p->have_exec = true;
-  return TURBOFFT_SUCCESS;
+  return exec_on_stream(p, in, out, p->d_scratch, s);
 }
 
 turbofft_status turbofft_exec_host(turbofft_plan* p, const void* host_in, void* host_out, turbofft_stream stream) {
@@ -1523,32 +1520,12 @@ int plan_device(const turbofft_plan* p) { return p->device; }
 void plan_set_error(turbofft_plan* p, const char* msg) { p->last_error = msg; }
 
 turbofft_status exec_given_scratch(turbofft_plan* p, const void* in, void* out, void* scratch, cudaStream_t s) {
-  if (!p || !in || !out) return TURBOFFT_INVALID_VALUE;
+  if (!p) return TURBOFFT_INVALID_VALUE;
   if (p->ragged) return TURBOFFT_UNSUPPORTED;
-  if (!aligned16(in) || !aligned16(out)) return TURBOFFT_INVALID_VALUE;
   if (p->scratch_bytes > 0 && (!scratch || !aligned16(scratch))) return TURBOFFT_INVALID_VALUE;
-  const size_t bytes = (size_t)(p->batch * p->n) * elem_bytes(p->dtype);
-  const char* a = static_cast<const char*>(in);
-  const char* b = static_cast<const char*>(out);
-  if (a < b + bytes && b < a + bytes) return TURBOFFT_UNSUPPORTED;
-  const bool ft = p->ft_mode != TURBOFFT_FT_OFF;
-  if (ft) {
-    cudaError_t e = cudaMemsetAsync(p->d_fts, 0, tf::FT_HEADER_BYTES, s);
-    if (e != cudaSuccess) return cuda_fail(p, e, "report reset");
-  }
-  tf::InjectSite inj = p->armed;
-  p->armed.active = 0;
-  p->nprof = 0;
-  turbofft_status st = run(p, in, out, scratch, p->batch, 0, s, inj);
+  turbofft_status st = check_io(p, in, out);
   if (st != TURBOFFT_SUCCESS) return st;
-  if (ft) {
-    cudaError_t e = cudaMemcpyAsync(p->h_fts, p->d_fts, sizeof(FtState), cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return cuda_fail(p, e, "report copy");
-  }
-  cudaError_t e = cudaEventRecord(p->done, s);
-  if (e != cudaSuccess) return cuda_fail(p, e, "event record");
-  p->have_exec = true;
-  return TURBOFFT_SUCCESS;
+  return exec_on_stream(p, in, out, scratch, s);
 }
 
 }  // namespace tf
