@@ -607,9 +607,13 @@ def run_ours(args):
     sweep = []
     for i, (dt2, eb2, d2, n2) in enumerate(cfgs):
         b = 2.0 * ELEMENTS * eb2
+        inf2 = plans_ft[(dt2, d2, n2)].info()
         sweep.append([dt2[5:], d2[:3], int(math.log2(n2)), round(b / (per_ft[i] * 1e-3) / 1e9, 1),
                       round(b / (per_plain[i] * 1e-3) / 1e9, 1),
-                      round(5.0 * ELEMENTS * math.log2(n2) / (per_ft[i] * 1e-3) / 1e9, 1)])
+                      round(5.0 * ELEMENTS * math.log2(n2) / (per_ft[i] * 1e-3) / 1e9, 1),
+                      round(b / (per_ft[i] * 1e-3) / 1e9 / peaks["hbm_gbs"], 3),
+                      "cl%d" % inf2["cluster"] if inf2["cluster"] else "x".join(
+                          str(inf2["sub_n"][q]) for q in range(inf2["num_passes"]))])
     per_dtype = {}
     for dt2, eb2 in DTYPES:
         idx = [i for i, c in enumerate(cfgs) if c[0] == dt2]
@@ -633,7 +637,8 @@ def run_ours(args):
                 "abft_overhead_pct": round(100.0 * (ms_ft / ms_plain - 1.0), 2),
                 "false_alarms_last_step": fa,
                 "per_dtype": per_dtype,
-                "sweep_columns": ["dtype", "dir", "log2N", "ft_GBs", "plain_GBs", "ft_GFLOPs"],
+                "sweep_columns": ["dtype", "dir", "log2N", "ft_GBs", "plain_GBs", "ft_GFLOPs", "ft_hbm_frac",
+                                  "passes"],
                 "sweep": sweep,
                 "ragged": ragged,
                 "spectral_filter": sfilter}

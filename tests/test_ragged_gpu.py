@@ -299,3 +299,20 @@ def test_ragged_full_size_sampled():
             got = yd[o:o + n].cpu().numpy()[None]
             assert float(oracle.rel_l2(got, ref)[0]) <= oracle.tolerance(np.float32, int(n)), (int(n), int(i))
     plan.close()
+
+
+def test_autotune_structure_choice_stays_correct():
+    """With autotuning on, a float32 2^14 plan times its split and cluster
+    structures and keeps the faster; either way the result is the transform."""
+    n, batch = 1 << 14, 40
+    x = ss.uniform_complex(29, batch, n, np.float32)
+    tfl.set_autotune(True)
+    try:
+        plans = [tfl.Plan(n, batch, "complex64", "forward", ft) for ft in ("off", "correct")]
+    finally:
+        tfl.set_autotune(False)
+    for p in plans:
+        assert p.info()["autotuned"] == 1
+        y = p.exec(torch.from_numpy(x).cuda()).cpu().numpy()
+        assert float(np.max(oracle.rel_l2(y, oracle.fft(x)))) <= oracle.tolerance(np.float32, n)
+        p.close()
