@@ -18,6 +18,10 @@ LIB = os.path.join(HERE, "libturbofft.so")
 
 SOURCES = [
     "tf_capi.cu",
+    "tf_tables.cu",
+    "tf_launch.cu",
+    "tf_autotune.cu",
+    "tf_ragged.cu",
     "tf_noalloc.cu",
     "tf_k_f32_sp.cu",
     "tf_k_f32_col.cu",
