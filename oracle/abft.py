@@ -19,7 +19,7 @@ The method (TurboFFT):
     y_k <- y_k - Delta corrects it (Sec. 4.1.1; delayed, batched correction of
     Sec. 4.1.2: the group is checked once, after all its signals).
 
-Readings where the paper is silent (each listed in the design doc):
+Readings where the paper is silent:
   * e: seeded unit-modulus random phases (default) or Wang's
     e_j = omega_3^j (Sec. 2.2.2) or all ones.
   * detection threshold: |S1| > tau with

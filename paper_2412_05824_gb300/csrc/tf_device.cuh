@@ -895,7 +895,6 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
           }
         }
       } else {
-#pragma unroll
         if constexpr (sizeof(R) == 4) {
           // energy (re^2, im^2) as one paired FP32 FMA per value
           float2 e2 = make_float2(0.f, 0.f);
