@@ -205,9 +205,11 @@ template <class K, int p> struct PassInfo {
 
 // Shared-memory index of (slot, pos) in the exchange written by pass p.
 // Slot-major layouts XOR bits [l, B) of the position with bits
-// [l + r, l + r + B - l) when the pass writes with a stride (l < B): a
-// padding-free swizzle that keeps both the pass's scattered writes and the
-// next pass's contiguous reads free of bank conflicts (Sec. 3.2).
+// [l + r, l + r + B - l) when the pass writes with a stride (l < B), and,
+// when a slot's threads cover less than a 128-byte bank row, add a per-slot
+// offset: a padding-free swizzle that keeps both the pass's scattered
+// writes and the next pass's contiguous reads free of bank conflicts
+// (Sec. 3.2).
 template <class K, int p> __device__ __forceinline__ int sidx(int slot, int pos) {
   if constexpr (K::SLOT_FAST) {
     // Position-major rows of S values.  When a 128-byte bank row holds
@@ -231,7 +233,11 @@ template <class K, int p> __device__ __forceinline__ int sidx(int slot, int pos)
   } else {
     constexpr int l = PassInfo<K, p>::LOG_L, r = PassInfo<K, p>::LOG_R;
     int q = pos;
-    if constexpr (l < K::B && l + r >= K::B) q ^= ((pos >> (l + r)) & ((1 << (K::B - l)) - 1)) << l;
+    if constexpr (l < K::B) q ^= ((pos >> (l + r)) & ((1 << (K::B - l)) - 1)) << l;
+    // when a slot's P threads span less than a bank row, the 32/P slots of a
+    // warp take different parts of it
+    constexpr int RUN = K::P * (int)sizeof(typename K::c);
+    if constexpr (K::P < 32 && RUN < 128 && K::NS >= (1 << K::B)) q ^= (slot % (128 / RUN)) * K::P;
     return slot * K::NS + q;
   }
 }
