@@ -92,6 +92,24 @@ __device__ __forceinline__ float abs_as_float(double v) {
   return __uint_as_float(((unsigned)fe << 23) | (((unsigned)hi & 0xFFFFFu) << 3));
 }
 
+// Power-of-two scaling of a double by integer operations.  For s = 2^-k,
+// v * s only lowers the exponent field by k when the result stays normal,
+// and a zero stays the same; pow2_scalable says whether v is such a value
+// (then pow2_scale gives bit for bit the floating-point product), else
+// (subnormal result, infinity, NaN) the caller multiplies.
+__device__ __forceinline__ int scaled_exponent_shift(double s) {
+  return 1023 - ((__double2hiint(s) >> 20) & 0x7FF);
+}
+__device__ __forceinline__ bool pow2_scalable(double v, int k) {
+  const int hi = __double2hiint(v);
+  const int ex = (hi >> 20) & 0x7FF;
+  return (ex > k && ex < 0x7FF) || ((hi & 0x7FFFFFFF) | __double2loint(v)) == 0;
+}
+__device__ __forceinline__ double pow2_scale(double v, int k) {
+  const int hi = __double2hiint(v);
+  return ((hi >> 20) & 0x7FF) == 0 ? v : __hiloint2double(hi - (k << 20), __double2loint(v));
+}
+
 template <typename C> __device__ __forceinline__ unsigned long long sign_mask(int on) {
   return on ? (sizeof(decltype(C::x)) == 4 ? 0x80000000ull : 0x8000000000000000ull) : 0ull;
 }
@@ -671,7 +689,17 @@ template <class K> struct StageSwz {
   static constexpr bool ON = !K::SLOT_FAST && K::P < 32 && RUN < 128 && (K::P % EPC) == 0;
   static constexpr int M = ON ? 128 / RUN : 1;
   static __device__ __forceinline__ int x(int slot) { return ON ? (slot % M) * K::P : 0; }
-  static __device__ __forceinline__ int chunk(int slot, int j) { return ON ? (j ^ (x(slot) / EPC)) : j; }
+  // One thread per float32 transform (P = 1): the thread reads its values
+  // as 16-byte pairs, and whole chunks are XOR-swizzled by slot so that the
+  // 8 threads of a quarter warp read 8 different 16-byte bank groups.
+  static constexpr bool PAIRS = !K::SLOT_FAST && K::P == 1 && EPC == 2;
+  static constexpr int U = K::NS / 2;              // chunks per transform
+  static constexpr int UM = U < 8 ? U : 8;
+  static constexpr int SPAN = U < 8 ? 8 / U : 1;   // slots that share 8 chunks
+  static __device__ __forceinline__ int chunk(int slot, int j) {
+    if constexpr (PAIRS) return j ^ ((slot / SPAN) % UM);
+    return ON ? (j ^ (x(slot) / EPC)) : j;
+  }
 };
 
 // XOR swizzle of the row pass's transposed store through shared memory
@@ -853,12 +881,23 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
     const bool valid = sig >= 0;
     c a[E];
     // ---- home positions from the staged tile
+    if constexpr (StageSwz<K>::PAIRS) {
+      const float4* s4 = reinterpret_cast<const float4*>(sm) + slot * (K::NS / 2);
 #pragma unroll
-    for (int i = 0; i < E; ++i) {
-      c v = mk<c>(0, 0);
-      const int pos = t + i * P;
-      if (valid) v = K::SLOT_FAST ? sm[pos * S + slot] : sm[slot * K::NS + (pos ^ StageSwz<K>::x(slot))];
-      a[i] = conj_mask(v, mask_in);
+      for (int j = 0; j < E / 2; ++j) {
+        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (valid) q = s4[StageSwz<K>::chunk(slot, j)];
+        a[2 * j] = conj_mask(make_float2(q.x, q.y), mask_in);
+        a[2 * j + 1] = conj_mask(make_float2(q.z, q.w), mask_in);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        c v = mk<c>(0, 0);
+        const int pos = t + i * P;
+        if (valid) v = K::SLOT_FAST ? sm[pos * S + slot] : sm[slot * K::NS + (pos ^ StageSwz<K>::x(slot))];
+        a[i] = conj_mask(v, mask_in);
+      }
     }
     __syncthreads();  // the tile is consumed; the stage becomes the exchange buffer
     // ---- input side of the checksums
@@ -962,8 +1001,26 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
     }
     // ---- store (scaled inverse: one uniform branch around the scaling)
     if (scaled) {
+      if constexpr (sizeof(R) == 8 && K::KIND != KIND_COL) {  // (a column pass is never last)
+        // the scale 2^-k only lowers exponents: where every value of the
+        // warp is zero or keeps a normal result, subtract k from the
+        // exponent fields with integer operations (the same bits as the
+        // product) and leave the float64 pipe to the transform
+        const int scale_log2 = scaled_exponent_shift(A.out_scale);  // 1/N = 2^-scale_log2
+        bool slow = false;
 #pragma unroll
-      for (int i = 0; i < E; ++i) a[i] = cscale(a[i], A.out_scale);
+        for (int i = 0; i < E; ++i) slow |= !pow2_scalable(a[i].x, scale_log2) || !pow2_scalable(a[i].y, scale_log2);
+        if (__any_sync(0xffffffffu, slow)) {
+#pragma unroll
+          for (int i = 0; i < E; ++i) a[i] = cscale(a[i], A.out_scale);
+        } else {
+#pragma unroll
+          for (int i = 0; i < E; ++i) a[i] = mk<c>(pow2_scale(a[i].x, scale_log2), pow2_scale(a[i].y, scale_log2));
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < E; ++i) a[i] = cscale(a[i], A.out_scale);
+      }
     }
     if constexpr (K::KIND == KIND_ROW) {
       // transposed store: rows r0..r0+S-1 are contiguous in the output for a
@@ -985,11 +1042,21 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
     } else {
       if (valid) {
         c* const ob = A.out + out_base<K>(g, sig);
-        const long long os = out_step<K>(g);
+        if constexpr (StageSwz<K>::PAIRS) {
+          // one thread per contiguous transform: 16-byte stores
+          static_assert(K::KIND == KIND_SP, "paired stores need a contiguous transform");
 #pragma unroll
-        for (int i = 0; i < E; ++i) {
-          const c v = conj_mask(a[i], mask_out);
-          __stcs(ob + (t + i * P) * os, v);
+          for (int j = 0; j < E / 2; ++j) {
+            const c v0 = conj_mask(a[2 * j], mask_out), v1 = conj_mask(a[2 * j + 1], mask_out);
+            __stcs(reinterpret_cast<float4*>(ob) + j, make_float4(v0.x, v0.y, v1.x, v1.y));
+          }
+        } else {
+          const long long os = out_step<K>(g);
+#pragma unroll
+          for (int i = 0; i < E; ++i) {
+            const c v = conj_mask(a[i], mask_out);
+            __stcs(ob + (t + i * P) * os, v);
+          }
         }
       }
     }

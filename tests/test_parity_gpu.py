@@ -77,6 +77,34 @@ def test_inverse_uniform(dt, direction, n):
 
 
 @pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("n", [8, 64, 4096, 1 << 14, 1 << 22])
+def test_scaled_inverse_is_exact_power_of_two_scaling(dt, n):
+    """The scaled inverse is the unscaled inverse times 2^-log2(N), bit for
+    bit, whichever way the kernel applies the scale: rows of ordinary
+    values, exact zeros, values whose scaled result is subnormal, subnormal
+    inputs, infinities and NaNs (the last ones must not change a transform's
+    neighbours either)."""
+    rdt = DT[dt]
+    batch = max(4, min(64, (1 << 18) // n))
+    x = ss.uniform_complex(11, batch, n, rdt)
+    tiny = np.finfo(rdt).tiny
+    x[1] = 0
+    x[2] *= tiny * 4          # outputs near the bottom of the normal range
+    x[3] *= tiny / 1024       # subnormal inputs
+    if batch > 5:
+        x[5, n // 3] = np.inf
+        x[5, n // 2] = complex(np.nan, 1.0)
+    ys, _ = run_gpu(x, "inverse")
+    yu, _ = run_gpu(x, "inverse_unscaled")
+    scale = rdt(1.0) / rdt(n)
+    with np.errstate(all="ignore"):
+        want = (yu.view(rdt) * scale).view(yu.dtype)
+    np.testing.assert_array_equal(ys.view(rdt), want.view(rdt))
+    ok = [r for r in range(batch) if r != 5]
+    assert np.all(np.isfinite(ys[ok]))
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
 @pytest.mark.parametrize("kind", ["impulse", "constant", "tone"])
 @pytest.mark.parametrize("n", [8, 32, 256, 2048, 1 << 14, 1 << 16, 1 << 21])
 def test_structured_inputs(dt, kind, n):
