@@ -548,6 +548,11 @@ template <typename R> struct PassArgs {
   const float4* vv4;  // float32 plans: v arranged the same way
   const c* tlo;   // inter-pass twiddles (KIND_COL)
   const c* thi;
+  // float64 column passes: the inter-pass twiddles, and the output-side
+  // checksum weights e_k1 conj(w), in the pass's access order
+  // (colw[n2 * NS + k1] = w^{k1 n2}); null otherwise
+  const c* colw;
+  const c* colwe;
   Geo geo;
   long long num_units;
   int conj_in;    // inverse: conjugate on load (first pass)
@@ -563,6 +568,21 @@ template <typename R> struct PassArgs {
   int rec_stride; // complex elements per record half (NS_MAX)
   InjectSite inj;
 };
+
+// column n2 of a column-pass signal (within its transform)
+template <class K> __device__ __forceinline__ long long col_of(const Geo& g, long long sig) {
+  return sig - (sig / g.n2) * g.n2;
+}
+// inter-pass twiddle of a column pass: from the float64 table in access
+// order, else the product of the two small tables
+template <class K>
+__device__ __forceinline__ typename K::c col_w(const PassArgs<typename K::real>& A, long long sig, int k1) {
+  if constexpr (sizeof(typename K::real) == 8) {
+    return ldg(A.colw + col_of<K>(A.geo, sig) * K::NS + k1);
+  } else {
+    return colTwiddle<K>(A.geo, A.tlo, A.thi, sig, k1);
+  }
+}
 
 // ---------------------------------------------------------------------------
 // block reduction helpers for the checksum group
@@ -979,10 +999,19 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
       for (int i = 0; i < E; ++i) {
         const int pos = t + i * P;
         if constexpr (K::KIND == KIND_COL) {
-          const c w = colTwiddle<K>(g, A.tlo, A.thi, valid ? sig : 0, pos);
           if constexpr (EAGER) ys[i] = cadd(ys[i], a[i]);
-          a[i] = cmul(a[i], w);
-          if constexpr (FT) cmac(pout, cmulconj(weight<K>(evp, pos), w), a[i]);
+          if constexpr (sizeof(R) == 8) {
+            // float64 is bound by its FP64 pipe: the twiddle and the
+            // checksum weight come from tables in access order (coalesced
+            // loads) instead of two complex products per value
+            const long long cw = col_of<K>(g, valid ? sig : 0) * K::NS + pos;
+            a[i] = cmul(a[i], ldg(A.colw + cw));
+            if constexpr (FT) cmac(pout, ldg(A.colwe + cw), a[i]);
+          } else {
+            const c w = colTwiddle<K>(g, A.tlo, A.thi, valid ? sig : 0, pos);
+            a[i] = cmul(a[i], w);
+            if constexpr (FT) cmac(pout, cmulconj(weight<K>(evp, pos), w), a[i]);
+          }
         } else {
           if constexpr (EAGER) ys[i] = cadd(ys[i], a[i]);
           if constexpr (FT) cmac(pout, weight<K>(evp, pos), a[i]);
@@ -1245,7 +1274,7 @@ __device__ __forceinline__ void load_output_internal(const PassArgs<typename K::
     auto v = A.out[out_off<K>(A.geo, sig, pos)];
     v = cscale(v, (R)1 / A.out_scale);
     if (A.conj_out) v = cconj(v);
-    if constexpr (K::KIND == KIND_COL) v = cmul(v, cconj(colTwiddle<K>(A.geo, A.tlo, A.thi, sig, pos)));
+    if constexpr (K::KIND == KIND_COL) v = cmul(v, cconj(col_w<K>(A, sig, pos)));
     a[i] = v;
   }
 }
@@ -1257,7 +1286,7 @@ __device__ __forceinline__ void store_output_internal(const PassArgs<typename K:
   for (int i = 0; i < K::E; ++i) {
     const int pos = t + i * K::P;
     auto v = a[i];
-    if constexpr (K::KIND == KIND_COL) v = cmul(v, colTwiddle<K>(A.geo, A.tlo, A.thi, sig, pos));
+    if constexpr (K::KIND == KIND_COL) v = cmul(v, col_w<K>(A, sig, pos));
     if (A.conj_out) v = cconj(v);
     v = cscale(v, A.out_scale);
     A.out[out_off<K>(A.geo, sig, pos)] = v;

@@ -81,6 +81,8 @@ void fill_args(const turbofft_plan* p, int pi, const void* in, void* out, int64_
   A.vv4 = static_cast<const float4*>(pp.d_vv4);
   A.tlo = static_cast<const c*>(pp.d_tlo ? pp.d_tlo : p->d_tlo);
   A.thi = static_cast<const c*>(pp.d_thi ? pp.d_thi : p->d_thi);
+  A.colw = static_cast<const c*>(pp.d_colw);
+  A.colwe = static_cast<const c*>(pp.d_colwe);
   A.geo.n = pp.g_n;
   A.geo.n1 = pp.g_n1;
   A.geo.n2 = pp.g_n2;

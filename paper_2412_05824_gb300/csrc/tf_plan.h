@@ -130,6 +130,8 @@ struct PassPlan {
   int outer = 0;
   void* d_tlo = nullptr;  // inter-pass twiddles of a column pass over length g_n
   void* d_thi = nullptr;
+  void* d_colw = nullptr;   // float64 column pass: twiddles in access order (g_n entries)
+  void* d_colwe = nullptr;  // and e_k1 conj(w) (checksummed plans)
   void* d_tw = nullptr;
   void* d_ev = nullptr;
   void* d_vv = nullptr;
@@ -206,6 +208,7 @@ bool upload(turbofft_plan* p, void** dst, const std::vector<cld>& v) {
   return cudaMemcpy(*dst, t.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess;
 }
 bool upload_tables(turbofft_plan* p, PassPlan& pp);
+bool col_tables(turbofft_plan* p, PassPlan& pp, const void* tlo, const void* thi, bool weights);
 
 // ---------------------------------------------------------------------------
 // launches (tf_launch.cu)

@@ -120,4 +120,49 @@ bool upload_tables(turbofft_plan* p, PassPlan& pp) {
   return upload<double>(p, &pp.d_tw, tw) && upload<double>(p, &pp.d_ev, e) && upload<double>(p, &pp.d_vv, v);
 }
 
+namespace {
+// Inter-pass twiddles of a float64 column pass over length L = n1 * n2 in
+// the pass's access order: colw[n2 * n1 + k1] = w_L^{k1 n2}, the same
+// product of the two small tables that float32 column passes form per value,
+// and colwe = e_k1 conj(colw), the output-side checksum weight of a value
+// taken after its twiddle.
+__global__ void col_fill_kernel(double2* colw, double2* colwe, const double2* tlo, const double2* thi,
+                                const double2* ev, int n1, long long total) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long n2 = i / n1;
+    const int k1 = (int)(i - n2 * n1);
+    const unsigned q = (unsigned)k1 * (unsigned)n2;
+    const double2 a = thi[q >> 12], b = tlo[q & 4095u];
+    const double2 w = make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+    colw[i] = w;
+    if (colwe) {
+      const double2 e = ev[k1];
+      colwe[i] = make_double2(e.x * w.x + e.y * w.y, e.y * w.x - e.x * w.y);
+    }
+  }
+}
+}  // namespace
+
+bool col_tables(turbofft_plan* p, PassPlan& pp, const void* tlo, const void* thi, bool weights) {
+  const long long total = (long long)pp.g_n1 * pp.g_n2;
+  const size_t bytes = (size_t)total * sizeof(double2);
+  if (!dev_alloc(p, &pp.d_colw, bytes)) return false;
+  if (weights && !dev_alloc(p, &pp.d_colwe, bytes)) return false;
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const int threads = 256;
+  const long long want = (total + threads - 1) / threads;
+  const int blocks = (int)(want < 8192 ? want : 8192);
+  col_fill_kernel<<<blocks, threads, 0, st>>>(static_cast<double2*>(pp.d_colw), static_cast<double2*>(pp.d_colwe),
+                                              static_cast<const double2*>(tlo), static_cast<const double2*>(thi),
+                                              static_cast<const double2*>(pp.d_ev), pp.g_n1, total);
+  const bool ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
+  cudaStreamDestroy(st);
+  return ok;
+}
+
 }  // namespace tfh
