@@ -141,7 +141,12 @@ typedef struct {
   int32_t group_transactions; /* transactions of one thread block per checksum group */
   int32_t grid[3];          /* persistent thread blocks launched per pass */
   int32_t block[3];         /* threads per block per pass */
-  int64_t workspace_bytes;  /* device memory the plan owns or will allocate */
+  int64_t workspace_bytes;  /* device memory the plan owns or will allocate;
+                               float64 multi-pass plans include 16 bytes per
+                               point of each column pass's length (n, and
+                               n2 for the second pass of a three-pass plan)
+                               for its twiddle table, twice that with fault
+                               tolerance on (checksum weights) */
   int64_t scratch_bytes;    /* intermediate buffer of a two-pass plan (0 for one pass) */
   int32_t per_block[3];     /* transforms (SP) / columns / rows one block holds per transaction */
   int32_t num_members;      /* ragged plan: distinct sizes (member plans); 0 otherwise */

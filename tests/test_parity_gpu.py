@@ -198,6 +198,33 @@ def test_plan_info():
     assert p1.info()["num_passes"] == 1 and p1.info()["sub_n"][0] == 1024
 
 
+def test_float64_column_tables_are_plan_owned():
+    """float64 two-pass plans own an n-point twiddle table for the column
+    pass (and an n-point checksum-weight table with fault tolerance on),
+    counted in workspace_bytes and freed with the plan."""
+    n = 1 << 16
+    free0, _ = torch.cuda.mem_get_info()
+    off = tfl.Plan(n, 3, "complex128", "forward", "off")
+    ft = tfl.Plan(n, 3, "complex128", "forward", "correct")
+    io, ic = off.info(), ft.info()
+    assert io["num_passes"] == 2
+    assert io["workspace_bytes"] >= io["scratch_bytes"] + n * 16
+    assert ic["workspace_bytes"] >= ic["scratch_bytes"] + 2 * n * 16
+    x = ss.uniform_complex(12, 3, n, np.float64)
+    xd = torch.from_numpy(x).cuda()
+    ref = oracle.fft(x)
+    for y in (off.exec(xd).cpu().numpy(), ft.exec(xd).cpu().numpy()):
+        assert float(np.max(oracle.rel_l2(y, ref))) <= oracle.tolerance(np.float64, n)
+    assert ft.report()["detected"] == 0
+    off.close()
+    ft.close()
+    del xd
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 >= free0 - (1 << 20)
+
+
 def test_exec_host_matches_device_path():
     n, batch = 4096, 300
     x = ss.uniform_complex(9, batch, n, np.float32)
