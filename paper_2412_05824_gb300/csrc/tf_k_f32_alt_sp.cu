@@ -5,7 +5,7 @@
 namespace tf {
 const KernelEntry* entries_f32_alt_sp(int* count) {
   static const KernelEntry t[] = {
-      make_entry<Cfg<float, 16, 8, 64, KIND_SP>>(),    make_entry<Cfg<float, 16, 16, 128, KIND_SP>>(),
+      make_entry<Cfg<float, 16, 16, 64, KIND_SP>>(),   make_entry<Cfg<float, 16, 16, 128, KIND_SP>>(),
       make_entry<Cfg<float, 64, 16, 16, KIND_SP>>(),   make_entry<Cfg<float, 64, 8, 64, KIND_SP>>(),
       make_entry<Cfg<float, 128, 16, 32, KIND_SP>>(),  make_entry<Cfg<float, 128, 8, 16, KIND_SP>>(),
       make_entry<Cfg<float, 256, 16, 16, KIND_SP>>(),  make_entry<Cfg<float, 256, 8, 8, KIND_SP>>(),

@@ -4,7 +4,7 @@
 namespace tf {
 const KernelEntry* entries_f32_sp(int* count) {
   static const KernelEntry t[] = {
-      make_entry<Cfg<float, 8, 8, 64, KIND_SP>>(),      make_entry<Cfg<float, 16, 16, 64, KIND_SP>>(),
+      make_entry<Cfg<float, 8, 8, 64, KIND_SP>>(),      make_entry<Cfg<float, 16, 8, 64, KIND_SP>>(),
       make_entry<Cfg<float, 32, 8, 32, KIND_SP>>(),     make_entry<Cfg<float, 64, 8, 32, KIND_SP>>(),
       make_entry<Cfg<float, 128, 16, 16, KIND_SP>>(),   make_entry<Cfg<float, 256, 16, 8, KIND_SP>>(),
       make_entry<Cfg<float, 512, 16, 4, KIND_SP>>(),    make_entry<Cfg<float, 1024, 16, 2, KIND_SP>>(),
