@@ -75,6 +75,23 @@ def test_null_handles_are_rejected(L):
     assert L.turbofft_plan_create(64, 4, 0, -1, 0, None) == tfl.INVALID_VALUE
 
 
+def test_null_handles_are_rejected_by_the_other_calls(L):
+    assert L.turbofft_set_group_transactions(None, 4) == tfl.INVALID_VALUE
+    assert L.turbofft_set_workspace(None, None, 0) == tfl.INVALID_VALUE
+    assert L.turbofft_set_profiling(None, 1) == tfl.INVALID_VALUE
+    assert L.turbofft_get_kernel_times(None, None, 0, None) == tfl.INVALID_VALUE
+    assert L.turbofft_exec_static_scratch(None, None, None, None) == tfl.INVALID_VALUE
+    assert L.turbofft_last_error(None) == b""
+
+
+@pytest.mark.parametrize("structure", [-1, 4, 99])
+def test_structured_create_rejects_unknown_structures(L, structure):
+    h = ctypes.c_void_p(123)
+    st = L.turbofft_plan_create_structured(1 << 14, 4, 0, -1, 0, structure, ctypes.byref(h))
+    assert st == tfl.INVALID_VALUE
+    assert not h.value
+
+
 def test_no_gpu_reports_cuda_error_not_crash(L):
     import torch
     if torch.cuda.is_available():
