@@ -357,7 +357,11 @@ turbofft_status turbofft_get_kernel_times(turbofft_plan *plan, turbofft_kernel_t
  *   - Plans needing more than TURBOFFT_STATIC_SCRATCH_BYTES are rejected with
  *     TURBOFFT_INVALID_VALUE (message in turbofft_last_error); nothing runs.
  *   - The first call on a device looks up the array's device address (with
- *     that device current); make that first call before any stream capture.
+ *     that device current).  Under CUDA's lazy module loading that lookup
+ *     loads the part of the library that holds the array, and the 32 MiB is
+ *     reserved on the device then, not when the library is opened.  So make
+ *     the first call during set-up: before the device-memory budget is fixed
+ *     and before any stream capture.  Later calls allocate nothing.
  *   - All calls on a device share the array: calls whose kernels may overlap
  *     on the GPU (e.g. on unordered streams) race on it.  Its contents carry
  *     over between calls and need no clearing: every element is written
@@ -365,8 +369,25 @@ turbofft_status turbofft_get_kernel_times(turbofft_plan *plan, turbofft_kernel_t
  *   - in, out, stream: as turbofft_exec.
  */
 #define TURBOFFT_STATIC_SCRATCH_BYTES (32u << 20)
+/* The array size this library was built with (TURBOFFT_STATIC_SCRATCH_BYTES),
+ * for callers that load the library without its header. */
+extern const uint64_t turbofft_static_scratch_bytes;
 turbofft_status turbofft_exec_static_scratch(turbofft_plan *plan, const void *in, void *out,
                                              turbofft_stream stream);
+
+/*
+ * No counterpart in the paper: a calibration call for roofline figures.
+ *
+ * Measured fused multiply-add rate of the current device in the arithmetic
+ * of `dtype` (F32: float FMA, F64: double FMA), 2 flops per FMA: a loop of
+ * independent FMA chains over every SM, timed with CUDA events on `stream`
+ * for about `seconds` (0 < seconds <= 60) of launches of ~50 ms; the best
+ * launch's rate is written to *tflops (TFLOP/s).  Synchronous.  The float64
+ * transforms are bound by this rate on GPUs whose FP64 pipe is narrow.
+ * Errors: INVALID_VALUE (bad dtype, seconds or NULL tflops), CUDA_ERROR.
+ */
+turbofft_status turbofft_fma_peak(turbofft_dtype dtype, double seconds, turbofft_stream stream,
+                                  double *tflops);
 
 /* Free everything the plan owns.  NULL is a no-op.  Waits for the plan's
  * outstanding work first. */

@@ -87,9 +87,8 @@ EXPORTS = [
     "turbofft_set_workspace", "turbofft_set_profiling", "turbofft_get_kernel_times",
     "turbofft_exec_static_scratch", "turbofft_plan_create_ragged", "turbofft_plan_get_member_info",
     "turbofft_set_autotune", "turbofft_plan_create_structured", "turbofft_set_group_transactions",
+    "turbofft_fma_peak",
 ]
-
-STATIC_SCRATCH_BYTES = 32 << 20
 
 _lib = None
 
@@ -121,6 +120,7 @@ def lib() -> ctypes.CDLL:
     L.turbofft_set_workspace.argtypes = [vp, vp, ctypes.c_size_t]
     L.turbofft_set_profiling.argtypes = [vp, i32]
     L.turbofft_get_kernel_times.argtypes = [vp, ctypes.POINTER(KernelTime), i32, ctypes.POINTER(i32)]
+    L.turbofft_fma_peak.argtypes = [i32, ctypes.c_double, vp, ctypes.POINTER(ctypes.c_double)]
     L.turbofft_status_string.argtypes = [i32]
     L.turbofft_status_string.restype = ctypes.c_char_p
     L.turbofft_last_error.argtypes = [vp]
@@ -130,6 +130,27 @@ def lib() -> ctypes.CDLL:
             getattr(L, name).restype = i32
     _lib = L
     return L
+
+
+def fma_peak(dtype="complex128", seconds: float = 0.5, stream=None) -> float:
+    """Measured FMA throughput (TFLOP/s) of the current device in the real
+    type of `dtype` (turbofft_fma_peak)."""
+    out = ctypes.c_double()
+    s = 0 if stream is None else stream.cuda_stream
+    _check(lib().turbofft_fma_peak(_dtype_code(dtype), float(seconds), s, ctypes.byref(out)), "turbofft_fma_peak")
+    return out.value
+
+
+def static_scratch_bytes() -> int:
+    """Size of the library's static scratch array (turbofft_static_scratch_bytes)."""
+    return int(ctypes.c_uint64.in_dll(lib(), "turbofft_static_scratch_bytes").value)
+
+
+def __getattr__(name):
+    # STATIC_SCRATCH_BYTES is read from the loaded library, not restated here
+    if name == "STATIC_SCRATCH_BYTES":
+        return static_scratch_bytes()
+    raise AttributeError(name)
 
 
 class TurboFFTError(RuntimeError):

@@ -23,6 +23,7 @@ SOURCES = [
     "tf_autotune.cu",
     "tf_ragged.cu",
     "tf_noalloc.cu",
+    "tf_peaks.cu",
     "tf_k_f32_sp.cu",
     "tf_k_f32_col.cu",
     "tf_k_f32_row.cu",

@@ -31,7 +31,9 @@ namespace {
 static __device__ __align__(256) unsigned char g_static_scratch[TURBOFFT_STATIC_SCRATCH_BYTES];
 
 // Device address of g_static_scratch per device, looked up once per device
-// (with that device current) on the first call that needs it.
+// (with that device current) on the first call that needs it.  With lazy
+// module loading the lookup is what loads this file's module, so the 32 MiB
+// is reserved on the device at that first call.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
@@ -63,6 +65,8 @@ turbofft_status scratch_address(int device, void** out) {
 }
 
 }  // namespace
+
+extern "C" const uint64_t turbofft_static_scratch_bytes = TURBOFFT_STATIC_SCRATCH_BYTES;
 
 extern "C" turbofft_status turbofft_exec_static_scratch(turbofft_plan* plan, const void* in, void* out,
                                                         turbofft_stream stream) {

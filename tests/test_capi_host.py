@@ -143,3 +143,22 @@ def test_ragged_odd_offset_is_fine_for_complex128(L):
         pytest.skip("a GPU is present")
     st, h = _ragged(L, [64, 128], [1, 65], dtype=1)
     assert st == tfl.CUDA_ERROR and not h.value
+
+
+def test_static_scratch_size_is_exported(L):
+    """The static scratch size comes from the library itself, and matches
+    the header's TURBOFFT_STATIC_SCRATCH_BYTES."""
+    src = open(HEADER).read()
+    m = re.search(r"#define TURBOFFT_STATIC_SCRATCH_BYTES \((\d+)u << (\d+)\)", src)
+    assert m, "header macro not found"
+    assert "extern const uint64_t turbofft_static_scratch_bytes;" in src
+    assert tfl.static_scratch_bytes() == int(m.group(1)) << int(m.group(2))
+    assert tfl.STATIC_SCRATCH_BYTES == tfl.static_scratch_bytes()
+
+
+def test_fma_peak_rejects_bad_arguments(L):
+    out = ctypes.c_double()
+    assert L.turbofft_fma_peak(0, 0.5, None, None) == tfl.INVALID_VALUE
+    assert L.turbofft_fma_peak(0, 0.0, None, ctypes.byref(out)) == tfl.INVALID_VALUE
+    assert L.turbofft_fma_peak(0, 100.0, None, ctypes.byref(out)) == tfl.INVALID_VALUE
+    assert L.turbofft_fma_peak(5, 0.5, None, ctypes.byref(out)) == tfl.INVALID_VALUE

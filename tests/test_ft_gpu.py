@@ -103,7 +103,7 @@ def test_mantissa_flips(dt, n, batch):
     r = Runner(n, batch, dt)
     rng = np.random.default_rng(3 * n + batch)
     bits = list(range(10, 21)) if dt == "c64" else list(range(40, 51))
-    escapes = 0
+    escapes = []
     for (tr, p, st, el, comp, b) in _sites(r, rng, 24, bits):
         _, err_off, _ = r.run("off", (tr, p, st, el, comp), b)
         y, err, rep = r.run("correct", (tr, p, st, el, comp), b)
@@ -113,12 +113,12 @@ def test_mantissa_flips(dt, n, batch):
             assert rep["corrected"] >= 1 and rep["uncorrectable"] == 0, rep
             assert float(np.max(err)) <= r.tol
         elif breaking:
-            escapes += 1
-            # an escape can only sit just above the bar (low checksum sensitivity)
-            assert float(np.max(err_off)) < 10 * r.tol
+            # a fault left undetected although it breaks the bar: recorded
+            # with its site (the bar is 0 such escapes)
+            escapes.append(((tr, p, st, el, comp, b), float(np.max(err_off)) / r.tol))
         else:
             assert float(np.max(err)) <= r.tol
-    assert escapes <= 1
+    assert escapes == [], escapes
 
 
 @pytest.mark.parametrize("dt,n,batch", [("c64", 512, 50), ("c64", 1 << 15, 5), ("c128", 1024, 11)])
