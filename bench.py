@@ -728,9 +728,14 @@ def run_ours(args):
     study = None
     if args.study and rank == 0:
         from paper_2412_05824_gb300 import abft_study
-        study = {"roc": [abft_study.roc(1024, 2000, "complex64"), abft_study.roc(1024, 2000, "complex128")],
+        # ROC at several lengths (signals per length scaled so each exec
+        # stays small), and the ABFT level / group-size ablation
+        roc_cases = [(256, 2000), (1024, 2000), (4096, 1000), (1 << 16, 128)]
+        study = {"roc": [abft_study.roc(n, b, dt) for n, b in roc_cases for dt in ("complex64", "complex128")],
                  "group_size": [abft_study.ablation(n, dt) for n, dt in
-                                ((1024, "complex64"), (4096, "complex64"), (1024, "complex128"))]}
+                                ((8, "complex64"), (16, "complex64"), (32, "complex64"), (8, "complex128"),
+                                 (16, "complex128"), (1024, "complex64"), (4096, "complex64"),
+                                 (1024, "complex128"))]}
 
     launches_per_step = 0
     for dt2, eb2, d2, n2 in cfgs:

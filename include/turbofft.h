@@ -76,11 +76,19 @@ typedef enum {
   TURBOFFT_FT_OFF = 0,            /* plain FFT, no checksums */
   TURBOFFT_FT_DETECT = 1,         /* checksums fused; detect and locate, report only */
   TURBOFFT_FT_CORRECT = 2,        /* detect, locate and correct in place (Sec. 4.1.2) */
-  TURBOFFT_FT_CORRECT_REGISTERS = 3 /* CORRECT, with the right-side sums accumulated in
-                                       registers during the transform (the thread-level
-                                       accumulation of Sec. 4.3) instead of formed from the
-                                       untouched input and the stored output when a group
-                                       fails its check; same results, more registers */
+  TURBOFFT_FT_CORRECT_REGISTERS = 3, /* CORRECT, with the right-side sums accumulated in
+                                        registers during the transform (the thread-level
+                                        accumulation of Sec. 4.3) instead of formed from the
+                                        untouched input and the stored output when a group
+                                        fails its check; same results, more registers */
+  TURBOFFT_FT_CORRECT_THREAD = 4  /* thread-level ABFT (Sec. 4.2.1): for lengths whose
+                                     transform one thread holds whole (F32 N = 8, 16, 32;
+                                     F64 N = 8, 16), each thread checks its own transform
+                                     (v.x against e.y, threshold per transform) with no
+                                     block reduction and corrects a failing transform in
+                                     its registers by recomputing it from the staged input.
+                                     UNSUPPORTED for other lengths, other structures and
+                                     ragged plans */
 } turbofft_ft_mode;
 
 typedef struct turbofft_plan turbofft_plan;

@@ -37,6 +37,7 @@ FT_OFF = 0
 FT_DETECT = 1
 FT_CORRECT = 2
 FT_CORRECT_REGISTERS = 3
+FT_CORRECT_THREAD = 4
 
 _DIRS = {"forward": FORWARD, "inverse": INVERSE, "inverse_unscaled": INVERSE_UNSCALED,
          "forward_scaled": FORWARD_SCALED, FORWARD: FORWARD, INVERSE: INVERSE,
@@ -46,8 +47,9 @@ STRUCTURE_CLUSTER = 2
 STRUCTURE_THREE_PASS = 3
 _STRUCT = {"split": STRUCTURE_SPLIT, "cluster": STRUCTURE_CLUSTER, "three_pass": STRUCTURE_THREE_PASS}
 _FT = {"off": FT_OFF, "detect": FT_DETECT, "correct": FT_CORRECT, "correct_registers": FT_CORRECT_REGISTERS,
+       "correct_thread": FT_CORRECT_THREAD,
        None: FT_OFF, False: FT_OFF, FT_OFF: FT_OFF, FT_DETECT: FT_DETECT, FT_CORRECT: FT_CORRECT,
-       FT_CORRECT_REGISTERS: FT_CORRECT_REGISTERS}
+       FT_CORRECT_REGISTERS: FT_CORRECT_REGISTERS, FT_CORRECT_THREAD: FT_CORRECT_THREAD}
 
 
 class Site(ctypes.Structure):

@@ -12,7 +12,9 @@ roc():       detection and false-alarm rates as the detection threshold is
              complex64, 5e-15 log2 N for complex128).
 ablation():  time of the transform with checksums for 1..16 transactions per
              checksum group against the plain transform (the thread-block
-             group-size study of Sec. 4.3, Figs. 16-17).
+             group-size study of Sec. 4.3, Figs. 16-17), with the
+             thread-level checks of Sec. 4.2.1 beside them where one thread
+             holds a whole transform.
 campaign():  the fault-injection campaign of Sec. 5.3: a run of launches in
              CORRECT mode on uniform[-1,1) signals in which 1 of every 100
              launches carries one seeded bit flip (an exponent bit, 30 / 62,
@@ -98,8 +100,10 @@ def roc(n: int = 1024, batch: int = 2000, dtype: str = "complex64", faults: int 
 
 
 def ablation(n: int, dtype: str = "complex64", elements: int = 1 << 26, groups=(1, 2, 4, 8, 16),
-             reps: int = 10) -> dict:
-    """ms per exec for each transactions-per-group setting against ABFT off."""
+             reps: int = 10, thread_level: bool = True) -> dict:
+    """ms per exec for each transactions-per-group setting (thread-block
+    level, TB-T) and, where the length allows it, for thread-level checks,
+    against ABFT off."""
     import torch
 
     import paper_2412_05824_gb300 as tfl
@@ -125,13 +129,27 @@ def ablation(n: int, dtype: str = "complex64", elements: int = 1 << 26, groups=(
     plain = tfl.Plan(n, batch, dtype, "forward", "off")
     base = timed(plain)
     plain.close()
-    ft = tfl.Plan(n, batch, dtype, "forward", "correct")
     rows = []
+    if thread_level:
+        # thread-level ABFT (Sec. 4.2.1) where one thread holds a whole
+        # transform; its plain baseline is the same one-thread shape
+        try:
+            tl = tfl.Plan(n, batch, dtype, "forward", "correct_thread")
+        except tfl.TurboFFTError:
+            tl = None
+        if tl is not None:
+            ms = timed(tl)
+            rows.append({"transactions": "thread", "ms": round(ms, 4),
+                         "overhead_pct": round(100.0 * (ms / base - 1.0), 2), "detected": tl.report()["detected"],
+                         "shape": "one thread per transform (radix %d)" % tl.info()["radix"][0]})
+            tl.close()
+    ft = tfl.Plan(n, batch, dtype, "forward", "correct")
     for t in groups:
         ft.set_group_transactions(t)
         ms = timed(ft)
         rows.append({"transactions": t, "ms": round(ms, 4), "overhead_pct": round(100.0 * (ms / base - 1.0), 2),
-                     "detected": ft.report()["detected"]})
+                     "detected": ft.report()["detected"],
+                     "shape": "%d threads per transform" % (n // ft.info()["radix"][0])})
     ft.close()
     return {"n": n, "dtype": dtype, "batch": batch, "plain_ms": round(base, 4), "rows": rows}
 

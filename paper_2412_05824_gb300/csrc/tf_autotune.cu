@@ -92,6 +92,7 @@ void autotune(turbofft_plan* p, const void* in, void* out, void* scratch) {
     const KernelEntry* best = nullptr;
     float best_ms = 0.f;
     for (const KernelEntry* ke : cands) {
+      if (!ke->main[ft_variant(p->ft_mode)]) continue;  // no kernel of this checksum variant
       if (!use_entry(p, pi, ke)) continue;
       bool ok = queue_plan(p, in, out, scratch, s, none) == TURBOFFT_SUCCESS;  // warm-up
       float ms_min = 0.f;

@@ -108,8 +108,12 @@ turbofft_status create_plan(int64_t n, int64_t batch, turbofft_dtype dtype, int 
       direction != TURBOFFT_FORWARD_SCALED)
     return TURBOFFT_INVALID_VALUE;
   if (ft_mode != TURBOFFT_FT_OFF && ft_mode != TURBOFFT_FT_DETECT && ft_mode != TURBOFFT_FT_CORRECT &&
-      ft_mode != TURBOFFT_FT_CORRECT_REGISTERS)
+      ft_mode != TURBOFFT_FT_CORRECT_REGISTERS && ft_mode != TURBOFFT_FT_CORRECT_THREAD)
     return TURBOFFT_INVALID_VALUE;
+  // thread-level checksums need one thread per whole transform: single-pass
+  // sizes only, and not inside a ragged plan
+  if (ft_mode == TURBOFFT_FT_CORRECT_THREAD && (structure == 2 || structure == 3 || t_ragged_member))
+    return TURBOFFT_UNSUPPORTED;
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -226,7 +230,7 @@ turbofft_status create_plan(int64_t n, int64_t batch, turbofft_dtype dtype, int 
   }
   for (int pi = 0; pi < p->num_passes && !p->cl; ++pi) {
     PassPlan& pp = p->pass[pi];
-    pp.ke = reg.find(dt, pp.kind, pp.ns);
+    pp.ke = reg.find_variant(dt, pp.kind, pp.ns, ft_variant(ft_mode));
     if (!pp.ke) {
       turbofft_destroy(p);
       return TURBOFFT_UNSUPPORTED;

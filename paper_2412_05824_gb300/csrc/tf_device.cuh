@@ -674,6 +674,11 @@ template <class K> constexpr bool paired_ft() {
   return false;  // measured slower on GB300: the 16-byte weights double the shared-memory traffic
 #endif
 }
+// Thread-level checksums (Sec. 4.2.1) apply where one thread holds a whole
+// transform: a single radix pass in registers, no shared-memory exchange.
+template <class K> constexpr bool thread_level_ok() {
+  return K::P == 1 && K::KIND == KIND_SP && K::NP == 1 && !paired_ft<K>();
+}
 template <class K> constexpr int ev_entry_bytes() { return paired_ft<K>() ? 16 : (int)sizeof(typename K::c); }
 template <class K> constexpr bool ev_in_smem() { return 2 * K::NS * ev_entry_bytes<K>() <= 32768; }
 // checksum weight `pos` (table in shared memory for small NS, else global)
@@ -815,7 +820,10 @@ __device__ __forceinline__ void atomic_max_nonneg(float* addr, float v) {
 // ---------------------------------------------------------------------------
 // FTM: 0 = no checksums; 1 = checksums, right-side sums formed on the rare
 // path from HBM; 2 = checksums, right-side sums kept in registers during the
-// pass (the thread-level accumulation of Sec. 4.3)
+// pass (the thread-level accumulation of Sec. 4.3); 3 = thread-level ABFT
+// (Sec. 4.2.1): every thread checks its own whole transform against a
+// per-transform threshold, with no block reduction; a failing transform is
+// recorded for the correction kernel, which recomputes it
 template <class K, int FTM>
 __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_FT : TwMode<K>::MINB)
     tf_pass_kernel(const PassArgs<typename K::real> A) {
@@ -824,6 +832,8 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
   constexpr int E = K::E, P = K::P, S = K::S;
   constexpr bool FT = FTM != 0;
   constexpr bool EAGER = FTM == 2;
+  constexpr bool TL = FTM == 3;
+  static_assert(!TL || thread_level_ok<K>(), "thread-level checksums need one thread per transform");
   extern __shared__ __align__(128) unsigned char smem_raw_[];
   char* smem_raw = reinterpret_cast<char*>(smem_raw_);
 
@@ -868,6 +878,7 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
   c xs[EAGER ? E : 1], ys[EAGER ? E : 1];
   R s1r = 0, s1i = 0, s2r = 0, s2i = 0, en = 0;
   int bad_lo = 0x7fffffff, bad_hi = -1;
+  unsigned checked = 0;           // transforms checked (thread-level mode)
   int gi = 0;                     // transaction index inside the group
   long long g_unit0 = blockIdx.x;
   long long groups = 0;
@@ -921,6 +932,7 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
     }
     __syncthreads();  // the tile is consumed; the stage becomes the exchange buffer
     // ---- input side of the checksums
+    if constexpr (TL) en = 0;  // per-transform threshold
     c pin = mk<c>(0, 0);
     if constexpr (FT) {
       if constexpr (paired_ft<K>()) {
@@ -1028,6 +1040,49 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
       }
       pout = mk<c>(q1.x - q2.y, q1.y + q2.x);
     }
+    // ---- thread-level check (one transform per thread, no block reduction)
+    if constexpr (TL) {
+      if (valid) {
+        ++checked;
+        const R rr = pout.x - pin.x, ri = pout.y - pin.y;
+        const R tau2 = tau_coef2 * (R)K::NS * en;
+        const R mag2 = rr * rr + ri * ri;
+        if (isfinite(mag2) && isfinite(tau2) && mag2 <= (R)0.5 * tau2) {
+          if (tau2 > 0) max_ratio2 = fmaxf(max_ratio2, (float)(mag2 / tau2));
+        } else {
+          // not clearly clean: the decision in float64
+          const double tau = A.tau_coef * sqrt((double)K::NS * (double)en);
+          const double mag = sqrt((double)rr * (double)rr + (double)ri * (double)ri);
+          if (isfinite(mag) && isfinite(tau) && mag <= tau) {
+            if (tau > 0) max_ratio2 = fmaxf(max_ratio2, (float)((mag / tau) * (mag / tau)));
+          } else {
+            // a record for the correction kernel that follows the pass: it
+            // recomputes this one transform from its untouched input
+            // (Delta = y - W x over a group of one) and checks it again
+            atomicAdd(&A.fts->detected, 1ull);
+            const unsigned long long r = atomicAdd(&A.fts->num_records, 1ull);
+            if (r < (unsigned long long)MAX_RECORDS) {
+              FtRecord& R0 = A.fts->rec[r];
+              R0.pass_id = A.pass_id;
+              R0.slot = slot;
+              R0.count = 1;
+              R0.located = 0;
+              R0.unit0 = unit;
+              R0.unit_stride = stride;
+              R0.transform_base = A.transform_base;
+              R0.s1r = rr; R0.s1i = ri; R0.s2r = rr; R0.s2i = ri;
+              R0.tau = tau;
+              R0.energy = en;
+              R0.result = FT_RES_PENDING;
+              R0.has_sums = 0;
+              R0.signal = -1;
+            } else {
+              atomicAdd(&A.fts->dropped, 1ull);
+            }
+          }
+        }
+      }
+    }
     // ---- store (scaled inverse: one uniform branch around the scaling)
     if (scaled) {
       if constexpr (sizeof(R) == 8 && K::KIND != KIND_COL) {  // (a column pass is never last)
@@ -1090,7 +1145,7 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
       }
     }
     // ---- per-transaction checksum residual, location encoding
-    if constexpr (FT) {
+    if constexpr (FT && !TL) {
       const R rr = pout.x - pin.x, ri = pout.y - pin.y;
       if (!(isfinite(rr) && isfinite(ri))) {
         bad_lo = min(bad_lo, gi);
@@ -1103,7 +1158,7 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
     }
     ++gi;
     const bool group_end = (gi == A.T) || (unit + stride >= A.num_units);
-    if constexpr (FT) {
+    if constexpr (FT && !TL) {
       if (group_end) {
         // ---- reduce the group over the threads of each slot.  Phase 1
         // reduces S1 and the energy in the working precision and clears
@@ -1238,7 +1293,16 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
       g_unit0 = unit + stride;
     }
   }
-  if constexpr (FT) {
+  if constexpr (TL) {
+    // every transform is its own check: count them, and the largest clean
+    // ratio, per warp
+    const unsigned total = __reduce_add_sync(0xffffffffu, checked);
+    const unsigned mr = __reduce_max_sync(0xffffffffu, __float_as_uint(sqrtf(max_ratio2)));
+    if ((tid & 31) == 0) {
+      if (total) atomicAdd(&A.fts->groups, (unsigned long long)total);
+      if (mr) atomic_max_nonneg(&A.fts->max_clean_ratio, __uint_as_float(mr));
+    }
+  } else if constexpr (FT) {
     if (tid == 0 && groups > 0) atomicAdd(&A.fts->groups, (unsigned long long)(groups * S));
     if (tid < S && max_ratio2 > 0.f) atomic_max_nonneg(&A.fts->max_clean_ratio, sqrtf(max_ratio2));
   }

@@ -35,6 +35,16 @@ template <class K> KernelEntry make_entry() {
   e.fn_main[1] = reinterpret_cast<const void*>(&tf_pass_kernel<K, 1>);
   e.fn_main[2] = reinterpret_cast<const void*>(&tf_pass_kernel<K, 2>);
   e.fn_fix = reinterpret_cast<const void*>(&tf_fix_kernel<K>);
+  // thread-level checksums exist where one thread holds a whole transform
+  if constexpr (thread_level_ok<K>()) {
+    e.smem_main[3] = pass_smem_bytes<K, 3>();
+    e.main[3] = &launch_main<K, 3>;
+    e.fn_main[3] = reinterpret_cast<const void*>(&tf_pass_kernel<K, 3>);
+  } else {
+    e.smem_main[3] = 0;
+    e.main[3] = nullptr;
+    e.fn_main[3] = nullptr;
+  }
   return e;
 }
 

@@ -24,7 +24,12 @@
 namespace tfh {
 
 // kernel variant of an ft_mode: 0 none, 1 checksums, 2 checksums + register sums
-int ft_variant(int ft_mode) { return ft_mode == TURBOFFT_FT_OFF ? 0 : (ft_mode == TURBOFFT_FT_CORRECT_REGISTERS ? 2 : 1); }
+int ft_variant(int ft_mode) {
+  if (ft_mode == TURBOFFT_FT_OFF) return 0;
+  if (ft_mode == TURBOFFT_FT_CORRECT_REGISTERS) return 2;
+  if (ft_mode == TURBOFFT_FT_CORRECT_THREAD) return 3;
+  return 1;
+}
 
 // cluster kernels have no register-sums variant: that mode runs as CORRECT
 int cl_variant(int ft_mode) { return ft_mode == TURBOFFT_FT_OFF ? 0 : 1; }
@@ -41,8 +46,8 @@ int occupancy_blocks(const KernelEntry* ke, int variant) {
 
 bool set_smem_attrs(const KernelEntry* ke) {
   // the attribute is per function; setting it again is harmless
-  for (int v = 0; v < 3; ++v)
-    if (cudaFuncSetAttribute(ke->fn_main[v], cudaFuncAttributeMaxDynamicSharedMemorySize, ke->smem_main[v]) !=
+  for (int v = 0; v < 4; ++v)
+    if (ke->fn_main[v] && cudaFuncSetAttribute(ke->fn_main[v], cudaFuncAttributeMaxDynamicSharedMemorySize, ke->smem_main[v]) !=
         cudaSuccess)
       return false;
   if (cudaFuncSetAttribute(ke->fn_fix, cudaFuncAttributeMaxDynamicSharedMemorySize, ke->smem_fix) != cudaSuccess)
@@ -99,7 +104,9 @@ void fill_args(const turbofft_plan* p, int pi, const void* in, void* out, int64_
   A.conj_out = (inverse && last) ? 1 : 0;
   A.out_scale = (last && scaled) ? (R)(1.0 / (double)p->n) : (R)1;
   A.tau_coef = pp.tau_coef * p->threshold_scale;
-  A.ft = p->ft_mode == TURBOFFT_FT_CORRECT_REGISTERS ? TURBOFFT_FT_CORRECT : p->ft_mode;
+  A.ft = (p->ft_mode == TURBOFFT_FT_CORRECT_REGISTERS || p->ft_mode == TURBOFFT_FT_CORRECT_THREAD)
+             ? TURBOFFT_FT_CORRECT
+             : p->ft_mode;
   A.T = p->T;
   A.pass_id = pi;
   A.transform_base = tbase;

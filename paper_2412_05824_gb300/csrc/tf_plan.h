@@ -58,6 +58,12 @@ struct Registry {
       if (e->dtype == dtype && e->kind == kind && e->ns == ns) return e;
     return nullptr;
   }
+  // first entry that has a kernel of checksum variant `variant`
+  const KernelEntry* find_variant(int dtype, int kind, int ns, int variant) const {
+    for (auto e : all)
+      if (e->dtype == dtype && e->kind == kind && e->ns == ns && e->main[variant]) return e;
+    return nullptr;
+  }
   std::vector<const KernelEntry*> find_all(int dtype, int kind, int ns) const {
     std::vector<const KernelEntry*> v;
     for (auto e : all)

@@ -119,6 +119,7 @@ turbofft_status turbofft_plan_create_ragged(const int64_t* sizes, const int64_t*
   if (direction != TURBOFFT_FORWARD && direction != TURBOFFT_INVERSE && direction != TURBOFFT_INVERSE_UNSCALED &&
       direction != TURBOFFT_FORWARD_SCALED)
     return TURBOFFT_INVALID_VALUE;
+  if (ft_mode == TURBOFFT_FT_CORRECT_THREAD) return TURBOFFT_UNSUPPORTED;  // one thread per transform only
   if (ft_mode != TURBOFFT_FT_OFF && ft_mode != TURBOFFT_FT_DETECT && ft_mode != TURBOFFT_FT_CORRECT &&
       ft_mode != TURBOFFT_FT_CORRECT_REGISTERS)
     return TURBOFFT_INVALID_VALUE;

@@ -15,11 +15,13 @@ struct KernelEntry {
   int s;            // sub-transforms per transaction
   int nt;           // threads per block
   int stages;       // radix passes
-  int smem_main[3]; // dynamic shared memory of the transform kernel per variant
+  int smem_main[4]; // dynamic shared memory of the transform kernel per variant
   int smem_fix;     // dynamic shared memory of the correction kernel
-  LaunchFn main[3];   // transform kernel: no checksums / checksums / checksums + register sums
+  // transform kernel: no checksums / checksums / checksums + register sums /
+  // thread-level checksums (one thread per transform only; null otherwise)
+  LaunchFn main[4];
   LaunchFn fix;       // correction kernel
-  const void* fn_main[3];
+  const void* fn_main[4];
   const void* fn_fix;
 };
 

@@ -162,3 +162,14 @@ def test_fma_peak_rejects_bad_arguments(L):
     assert L.turbofft_fma_peak(0, 0.0, None, ctypes.byref(out)) == tfl.INVALID_VALUE
     assert L.turbofft_fma_peak(0, 100.0, None, ctypes.byref(out)) == tfl.INVALID_VALUE
     assert L.turbofft_fma_peak(5, 0.5, None, ctypes.byref(out)) == tfl.INVALID_VALUE
+
+
+def test_thread_level_mode_rejected_where_it_cannot_apply(L):
+    h = ctypes.c_void_p()
+    sizes = (ctypes.c_int64 * 2)(8, 16)
+    offs = (ctypes.c_int64 * 2)(0, 8)
+    # ragged plans and cluster / three-pass structures have no one-thread shape
+    assert L.turbofft_plan_create_ragged(sizes, offs, 2, 0, -1, 4, ctypes.byref(h)) == tfl.UNSUPPORTED
+    assert L.turbofft_plan_create_structured(1 << 14, 4, 0, -1, 4, 2, ctypes.byref(h)) == tfl.UNSUPPORTED
+    assert L.turbofft_plan_create_structured(1 << 22, 1, 0, -1, 4, 3, ctypes.byref(h)) == tfl.UNSUPPORTED
+    assert L.turbofft_plan_create(64, 4, 0, -1, 5, ctypes.byref(h)) == tfl.INVALID_VALUE
