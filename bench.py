@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--campaign-sizes", default="8,9,10,11,12,13,14,15,16,17,18,19,20",
                     help="comma list of log2 N of the fault-injection campaign")
     ap.add_argument("--no-config1", action="store_true", help="skip the N=256 x 4096 float32 timing (config 1)")
+    ap.add_argument("--no-float-pairs", action="store_true",
+                    help="skip the float64 sweep in float-pair arithmetic (FT off) against the FP64-pipe kernels")
     return ap.parse_args()
 
 
@@ -479,6 +481,41 @@ def bench_campaign(args, peaks):
                              "plain-path output"}
 
 
+def bench_float_pairs(args, stream, peaks, x, y, workspace, sizes):
+    """float64 sweep with ABFT off: the float-pair plans (float64 data,
+    float arithmetic) against the FP64-pipe plans, same buffers, forward and
+    inverse, 2^28 elements per call."""
+    import paper_2412_05824_gb300 as tfl
+
+    rows = []
+    tot = {"fp64": 0.0, "pairs": 0.0}
+    nbytes = 2.0 * ELEMENTS * 16
+    for d in DIRECTIONS:
+        for n in sizes:
+            ms = {}
+            for arith, structure in (("fp64", "default"), ("pairs", "float_pairs")):
+                p = tfl.Plan(n, ELEMENTS // n, "complex128", d, "off", structure=structure)
+                p.set_workspace(workspace)
+
+                def f():
+                    st = p.exec_ptr(x.data_ptr(), y.data_ptr(), stream.cuda_stream)
+                    if st != tfl.SUCCESS:
+                        raise RuntimeError("exec failed: %d" % st)
+                ms[arith] = time_calls(f, args.warmup, max(args.steps, 3), stream)
+                tot[arith] += ms[arith]
+                p.close()
+            rows.append([d[:3], int(math.log2(n)), round(nbytes / (ms["fp64"] * 1e-3) / 1e9, 1),
+                         round(nbytes / (ms["pairs"] * 1e-3) / 1e9, 1), round(ms["fp64"] / ms["pairs"], 3),
+                         round(nbytes / (ms["pairs"] * 1e-3) / 1e9 / peaks["hbm_gbs"], 3)])
+    nall = nbytes * len(rows)
+    return {"workload": "float64 C2C, ABFT off, N=2^%d..2^%d, forward + inverse, 2^28 elements per call"
+                        % (int(math.log2(sizes[0])), int(math.log2(sizes[-1]))),
+            "columns": ["dir", "log2N", "fp64_GBs", "float_pairs_GBs", "speedup", "float_pairs_hbm_frac"],
+            "rows": rows,
+            "sweep_gbs": {k: round(nall / (v * 1e-3) / 1e9, 1) for k, v in tot.items()},
+            "speedup": round(tot["fp64"] / tot["pairs"], 3)}
+
+
 def bench_config1(args, dev, stream, peaks):
     """Config 1: plain float32 forward, N = 256, batch 4096 (8 MiB in, 8 MiB
     out).  The working set fits in L2, so it is timed two ways: over a
@@ -723,6 +760,9 @@ def run_ours(args):
 
     ragged = bench_ragged(args, dev, stream, rank, peaks) if not args.no_ragged else None
     config1 = bench_config1(args, dev, stream, peaks) if not args.no_config1 else None
+    f64_sizes = sorted({n for dt2, eb2, d2, n in cfgs if dt2 == "float64"})
+    float_pairs = (bench_float_pairs(args, stream, peaks, bufs["float64"][0], bufs["float64"][1], workspace,
+                                     f64_sizes) if (not args.no_float_pairs and f64_sizes) else None)
     campaign = bench_campaign(args, peaks) if (not args.no_campaign and rank == 0) else None
     sfilter = bench_filter(args, dev, stream) if not args.no_filter else None
     study = None
@@ -780,6 +820,7 @@ def run_ours(args):
                 "ragged": ragged,
                 "spectral_filter": sfilter,
                 "config1": config1,
+                "float64_float_pairs": float_pairs,
                 "ft_campaign": campaign,
                 "fp64_fma_peak_tflops": round(fp64_peak, 4) if fp64_peak else None}
         if study is not None:

@@ -84,7 +84,8 @@ typedef enum {
   TURBOFFT_FT_CORRECT_THREAD = 4  /* thread-level ABFT (Sec. 4.2.1): for lengths whose
                                      transform one thread holds whole (F32 N = 8, 16, 32;
                                      F64 N = 8, 16), each thread checks its own transform
-                                     (v.x against e.y, threshold per transform) with no
+                                     (v.x against e.y, per-transform threshold with
+                                     twice the group threshold's gamma) with no
                                      block reduction and corrects a failing transform in
                                      its registers by recomputing it from the staged input.
                                      UNSUPPORTED for other lengths, other structures and
@@ -205,12 +206,25 @@ turbofft_status turbofft_plan_create(int64_t n, int64_t batch, turbofft_dtype dt
  *                               default for float32 n >= 2^22); for n >= 2^9
  *                               where every pass has a kernel configuration,
  *                               else TURBOFFT_UNSUPPORTED
+ *   TURBOFFT_STRUCTURE_FLOAT_PAIRS  F64 only, ft_mode OFF only (else
+ *                               TURBOFFT_UNSUPPORTED): the SPLIT passes with
+ *                               the float64 data held in registers and
+ *                               shared memory as float pairs (hi + lo, 48
+ *                               significand bits) and transformed with float
+ *                               arithmetic instead of on the FP64 pipe
+ *                               (GB300 runs FP64 at about 1/64 of its FP32
+ *                               rate); the data in memory stays complex128.
+ *                               Inputs must lie in [2^-74, 2^127) in
+ *                               magnitude (or be zero): the float exponent
+ *                               range.  No counterpart in the paper (its
+ *                               GPUs run FP64 at 1/2 to 1/32 of FP32)
  * Every structure computes the same transform to the same accuracy bar.
  * Errors: as turbofft_plan_create; INVALID_VALUE for another structure.
  */
 #define TURBOFFT_STRUCTURE_SPLIT 1
 #define TURBOFFT_STRUCTURE_CLUSTER 2
 #define TURBOFFT_STRUCTURE_THREE_PASS 3
+#define TURBOFFT_STRUCTURE_FLOAT_PAIRS 4
 turbofft_status turbofft_plan_create_structured(int64_t n, int64_t batch, turbofft_dtype dtype,
                                                 int direction, turbofft_ft_mode ft_mode, int structure,
                                                 turbofft_plan **plan);

@@ -45,7 +45,9 @@ _DIRS = {"forward": FORWARD, "inverse": INVERSE, "inverse_unscaled": INVERSE_UNS
 STRUCTURE_SPLIT = 1
 STRUCTURE_CLUSTER = 2
 STRUCTURE_THREE_PASS = 3
-_STRUCT = {"split": STRUCTURE_SPLIT, "cluster": STRUCTURE_CLUSTER, "three_pass": STRUCTURE_THREE_PASS}
+STRUCTURE_FLOAT_PAIRS = 4
+_STRUCT = {"split": STRUCTURE_SPLIT, "cluster": STRUCTURE_CLUSTER, "three_pass": STRUCTURE_THREE_PASS,
+           "float_pairs": STRUCTURE_FLOAT_PAIRS}
 _FT = {"off": FT_OFF, "detect": FT_DETECT, "correct": FT_CORRECT, "correct_registers": FT_CORRECT_REGISTERS,
        "correct_thread": FT_CORRECT_THREAD,
        None: FT_OFF, False: FT_OFF, FT_OFF: FT_OFF, FT_DETECT: FT_DETECT, FT_CORRECT: FT_CORRECT,
@@ -184,7 +186,9 @@ class Plan:
                  structure="default"):
         """structure: "default" (chosen by the library), "split" (one pass or
         two four-step passes), "cluster" (one pass over thread-block
-        clusters) or "three_pass"."""
+        clusters), "three_pass", or "float_pairs" (complex128, ft "off":
+        the split passes in float-pair arithmetic instead of on the FP64
+        pipe)."""
         self.n, self.batch = int(n), int(batch)
         self.dtype_code = _dtype_code(dtype)
         self.direction = _DIRS[direction]

@@ -34,6 +34,7 @@ SOURCES = [
     "tf_k_f32_alt_cr.cu",
     "tf_k_f32_cl.cu",
     "tf_k_f64_alt.cu",
+    "tf_k_pairs.cu",
 ]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

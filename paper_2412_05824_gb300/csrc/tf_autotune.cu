@@ -64,7 +64,7 @@ void autotune(turbofft_plan* p, const void* in, void* out, void* scratch) {
     return;
   }
   const Registry& reg = registry();
-  const int dt = p->dtype == TURBOFFT_C2C_F32 ? 0 : 1;
+  const int dt = kernel_dtype(p);
   cudaStream_t s = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||

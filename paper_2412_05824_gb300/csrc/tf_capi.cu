@@ -114,6 +114,11 @@ turbofft_status create_plan(int64_t n, int64_t batch, turbofft_dtype dtype, int 
   // sizes only, and not inside a ragged plan
   if (ft_mode == TURBOFFT_FT_CORRECT_THREAD && (structure == 2 || structure == 3 || t_ragged_member))
     return TURBOFFT_UNSUPPORTED;
+  // float-pair arithmetic: float64 data, no checksums (its rounding is above
+  // the float64 detection threshold), not inside a ragged plan
+  const bool pairs = structure == TURBOFFT_STRUCTURE_FLOAT_PAIRS;
+  if (pairs && (dtype != TURBOFFT_C2C_F64 || ft_mode != TURBOFFT_FT_OFF || t_ragged_member))
+    return TURBOFFT_UNSUPPORTED;
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -132,7 +137,8 @@ turbofft_status create_plan(int64_t n, int64_t batch, turbofft_dtype dtype, int 
   p->direction = direction;
   p->ft_mode = ft_mode;
   p->device = dev;
-  const int dt = dtype == TURBOFFT_C2C_F32 ? 0 : 1;
+  p->pairs = pairs;
+  const int dt = kernel_dtype(p);
 
   // pass split: one pass up to the largest single-pass size, else N1 x N2
   // passes, or N1 x N2 x N3 for large float32 sizes (three passes whose
@@ -243,6 +249,7 @@ turbofft_status create_plan(int64_t n, int64_t batch, turbofft_dtype dtype, int 
     const int occ = occupancy_blocks(pp.ke, ft_variant(ft_mode));
     pp.grid = occ * g_num_sms;
     pp.tau_coef = kGamma[dt] * kUnitRoundoff[dt] * sqrt((double)ilog2_exact(pp.ns));
+    if (ft_mode == TURBOFFT_FT_CORRECT_THREAD) pp.tau_coef *= kThreadLevelGammaFactor;
     if (!upload_tables(p, pp)) {
       turbofft_destroy(p);
       return TURBOFFT_ALLOC_FAILED;
@@ -260,8 +267,9 @@ turbofft_status create_plan(int64_t n, int64_t batch, turbofft_dtype dtype, int 
       std::vector<cld> lo(4096), hi((size_t)std::max<int64_t>(1, L / 4096));
       for (int j = 0; j < 4096; ++j) lo[j] = root(L, j);
       for (size_t j = 0; j < hi.size(); ++j) hi[j] = root(L, (int64_t)j * 4096);
-      ok = (dt == 0) ? (upload<float>(p, lo_dst, lo) && upload<float>(p, hi_dst, hi))
-                     : (upload<double>(p, lo_dst, lo) && upload<double>(p, hi_dst, hi));
+      ok = (dt == 0)   ? (upload<float>(p, lo_dst, lo) && upload<float>(p, hi_dst, hi))
+           : (dt == 2) ? (upload_pairs(p, lo_dst, lo) && upload_pairs(p, hi_dst, hi))
+                       : (upload<double>(p, lo_dst, lo) && upload<double>(p, hi_dst, hi));
       if (ok && dt == 1 && !p->cl) ok = col_tables(p, p->pass[pi], *lo_dst, *hi_dst, ft_mode != TURBOFFT_FT_OFF);
     }
     p->scratch_bytes = p->cl ? 0 : (size_t)(batch * n) * elem_bytes(dtype);
@@ -349,7 +357,7 @@ turbofft_status turbofft_plan_create_structured(int64_t n, int64_t batch, turbof
                                                 turbofft_ft_mode ft_mode, int structure, turbofft_plan** out) {
   if (out) *out = nullptr;
   if (structure != TURBOFFT_STRUCTURE_SPLIT && structure != TURBOFFT_STRUCTURE_CLUSTER &&
-      structure != TURBOFFT_STRUCTURE_THREE_PASS)
+      structure != TURBOFFT_STRUCTURE_THREE_PASS && structure != TURBOFFT_STRUCTURE_FLOAT_PAIRS)
     return TURBOFFT_INVALID_VALUE;
   turbofft_status st = create_plan(n, batch, dtype, direction, ft_mode, structure, out);
   if (st == TURBOFFT_SUCCESS && structure == TURBOFFT_STRUCTURE_CLUSTER && !(*out)->cl) {

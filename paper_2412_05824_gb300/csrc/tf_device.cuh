@@ -42,6 +42,7 @@
 #include <type_traits>
 #include <utility>
 
+#include "tf_dd.cuh"
 #include "tf_dft_constants.h"
 #include "tf_types.h"
 
@@ -53,6 +54,7 @@ namespace tf {
 template <typename R> struct CT;
 template <> struct CT<float> { using c = float2; };
 template <> struct CT<double> { using c = double2; };
+template <> struct CT<dd> { using c = cdd; };  // float64 data in float-pair arithmetic
 
 template <typename C> __device__ __forceinline__ C mk(decltype(C::x) a, decltype(C::x) b) {
   C r; r.x = a; r.y = b; return r;
@@ -79,6 +81,10 @@ __device__ __forceinline__ float2 conj_mask(float2 v, unsigned long long m) {
 }
 __device__ __forceinline__ double2 conj_mask(double2 v, unsigned long long m) {
   return make_double2(v.x, __longlong_as_double(__double_as_longlong(v.y) ^ (long long)m));
+}
+__device__ __forceinline__ cdd conj_mask(cdd v, unsigned long long m) {
+  const unsigned f = m ? 0x80000000u : 0u;
+  return cdd{v.x, dd(__uint_as_float(__float_as_uint(v.y.hi) ^ f), __uint_as_float(__float_as_uint(v.y.lo) ^ f))};
 }
 // |v| of a double as a float built with integer operations from its
 // exponent and top 20 mantissa bits (relative error < 2^-20): for the energy
@@ -123,6 +129,19 @@ template <typename C> __device__ __forceinline__ void cmac(C& acc, C a, C b) {
 }
 
 template <typename C> __device__ __forceinline__ C ldg(const C* p) { return __ldg(p); }
+__device__ __forceinline__ cdd ldg(const cdd* p) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  return cdd{dd(v.x, v.y), dd(v.z, v.w)};
+}
+
+// Values of a staged input tile and of the global output.  Float-pair plans
+// keep float64 data in memory and float pairs in registers and in the
+// shared-memory exchanges: the tile is read as float64 and split, the
+// output joined back to float64.
+template <typename C> __device__ __forceinline__ C tile_val(const C* p) { return *p; }
+__device__ __forceinline__ cdd tile_val(const cdd* p) { return cdd_from(*reinterpret_cast<const double2*>(p)); }
+template <typename C> __device__ __forceinline__ void store_out(C* p, C v) { __stcs(p, v); }
+__device__ __forceinline__ void store_out(cdd* p, cdd v) { __stcs(reinterpret_cast<double2*>(p), cdd_to(v)); }
 
 template <int N> struct ILog2 { static constexpr int v = 1 + ILog2<N / 2>::v; };
 template <> struct ILog2<1> { static constexpr int v = 0; };
@@ -270,6 +289,8 @@ __device__ __forceinline__ float flip1(float f, int bit) { return __uint_as_floa
 __device__ __forceinline__ double flip1(double f, int bit) {
   return __longlong_as_double(__double_as_longlong(f) ^ (1ll << bit));
 }
+// a float pair stands for a float64 value: flip the bit of that value
+__device__ __forceinline__ dd flip1(dd f, int bit) { return dd_from_double(flip1(dd_to_double(f), bit)); }
 template <typename C> __device__ __forceinline__ void flip_bit(C& v, int comp, int bit) {
   if (comp) v.y = flip1(v.y, bit);
   else v.x = flip1(v.x, bit);
@@ -577,7 +598,7 @@ template <class K> __device__ __forceinline__ long long col_of(const Geo& g, lon
 // order, else the product of the two small tables
 template <class K>
 __device__ __forceinline__ typename K::c col_w(const PassArgs<typename K::real>& A, long long sig, int k1) {
-  if constexpr (sizeof(typename K::real) == 8) {
+  if constexpr (std::is_same<typename K::real, double>::value) {
     return ldg(A.colw + col_of<K>(A.geo, sig) * K::NS + k1);
   } else {
     return colTwiddle<K>(A.geo, A.tlo, A.thi, sig, k1);
@@ -669,7 +690,7 @@ template <class K> constexpr int stage_bytes() {
 // weights e by the inter-pass twiddle per element and keeps the scalar form
 template <class K> constexpr bool paired_ft() {
 #ifdef TF_PAIRED_CHECKSUMS
-  return sizeof(typename K::real) == 4;
+  return std::is_same<typename K::real, float>::value;
 #else
   return false;  // measured slower on GB300: the 16-byte weights double the shared-memory traffic
 #endif
@@ -926,7 +947,7 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
       for (int i = 0; i < E; ++i) {
         c v = mk<c>(0, 0);
         const int pos = t + i * P;
-        if (valid) v = K::SLOT_FAST ? sm[pos * S + slot] : sm[slot * K::NS + (pos ^ StageSwz<K>::x(slot))];
+        if (valid) v = tile_val(K::SLOT_FAST ? &sm[pos * S + slot] : &sm[slot * K::NS + (pos ^ StageSwz<K>::x(slot))]);
         a[i] = conj_mask(v, mask_in);
       }
     }
@@ -948,7 +969,7 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
         }
         pin = mk<c>(q1.x - q2.y, q1.y + q2.x);
         en += e2.x + e2.y;
-      } else if constexpr (sizeof(R) == 8) {
+      } else if constexpr (std::is_same<R, double>::value) {
         // float64: the energy only scales tau, so it is accumulated in
         // float32 from converted values, keeping the float64 pipe for the
         // transform and the checksum products
@@ -972,7 +993,7 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
           }
         }
       } else {
-        if constexpr (sizeof(R) == 4) {
+        if constexpr (std::is_same<R, float>::value) {
           // energy (re^2, im^2) as one paired FP32 FMA per value
           float2 e2 = make_float2(0.f, 0.f);
 #pragma unroll
@@ -1012,7 +1033,7 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
         const int pos = t + i * P;
         if constexpr (K::KIND == KIND_COL) {
           if constexpr (EAGER) ys[i] = cadd(ys[i], a[i]);
-          if constexpr (sizeof(R) == 8) {
+          if constexpr (std::is_same<R, double>::value) {
             // float64 is bound by its FP64 pipe: the twiddle and the
             // checksum weight come from tables in access order (coalesced
             // loads) instead of two complex products per value
@@ -1085,7 +1106,7 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
     }
     // ---- store (scaled inverse: one uniform branch around the scaling)
     if (scaled) {
-      if constexpr (sizeof(R) == 8 && K::KIND != KIND_COL) {  // (a column pass is never last)
+      if constexpr (std::is_same<R, double>::value && K::KIND != KIND_COL) {  // (a column pass is never last)
         // the scale 2^-k only lowers exponents: where every value of the
         // warp is zero or keeps a normal result, subtract k from the
         // exponent fields with integer operations (the same bits as the
@@ -1120,7 +1141,7 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
       for (int i = 0; i < E; ++i) {
         const int pos = t2 + i * P;
         const c v = conj_mask(sm[s2 * K::NS + (pos ^ tsw<K>(s2))], mask_out);
-        __stcs(ob + pos * os, v);  // streaming: keep L1 for the tables
+        store_out(ob + pos * os, v);  // streaming: keep L1 for the tables
       }
       __syncthreads();
     } else {
@@ -1139,7 +1160,7 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
 #pragma unroll
           for (int i = 0; i < E; ++i) {
             const c v = conj_mask(a[i], mask_out);
-            __stcs(ob + (t + i * P) * os, v);
+            store_out(ob + (t + i * P) * os, v);
           }
         }
       }

@@ -48,4 +48,28 @@ template <class K> KernelEntry make_entry() {
   return e;
 }
 
+// Float-pair plans have no checksums: only the plain transform kernel.
+template <class K> KernelEntry make_entry_plain() {
+  KernelEntry e;
+  e.dtype = 2;
+  e.kind = K::KIND;
+  e.ns = K::NS;
+  e.e = K::E;
+  e.s = K::S;
+  e.nt = K::NT;
+  e.stages = K::NP;
+  e.smem_main[0] = pass_smem_bytes<K, 0>();
+  e.main[0] = &launch_main<K, 0>;
+  e.fn_main[0] = reinterpret_cast<const void*>(&tf_pass_kernel<K, 0>);
+  for (int v = 1; v < 4; ++v) {
+    e.smem_main[v] = 0;
+    e.main[v] = nullptr;
+    e.fn_main[v] = nullptr;
+  }
+  e.smem_fix = 0;
+  e.fix = nullptr;
+  e.fn_fix = nullptr;
+  return e;
+}
+
 }  // namespace tf

@@ -31,6 +31,8 @@ int ft_variant(int ft_mode) {
   return 1;
 }
 
+int kernel_dtype(const turbofft_plan* p) { return p->dtype == TURBOFFT_C2C_F32 ? 0 : (p->pairs ? 2 : 1); }
+
 // cluster kernels have no register-sums variant: that mode runs as CORRECT
 int cl_variant(int ft_mode) { return ft_mode == TURBOFFT_FT_OFF ? 0 : 1; }
 
@@ -50,7 +52,8 @@ bool set_smem_attrs(const KernelEntry* ke) {
     if (ke->fn_main[v] && cudaFuncSetAttribute(ke->fn_main[v], cudaFuncAttributeMaxDynamicSharedMemorySize, ke->smem_main[v]) !=
         cudaSuccess)
       return false;
-  if (cudaFuncSetAttribute(ke->fn_fix, cudaFuncAttributeMaxDynamicSharedMemorySize, ke->smem_fix) != cudaSuccess)
+  if (ke->fn_fix &&
+      cudaFuncSetAttribute(ke->fn_fix, cudaFuncAttributeMaxDynamicSharedMemorySize, ke->smem_fix) != cudaSuccess)
     return false;
   return true;
 }
@@ -218,6 +221,10 @@ turbofft_status run(turbofft_plan* p, const void* in, void* out, void* scratch, 
       fill_args<float>(p, pi, pin, pout, batch, tbase, inj, A);
       timed(2 * pi, [&] { pp.ke->main[ft_variant(p->ft_mode)](&A, grid, stream); });
       if (ft) timed(2 * pi + 1, [&] { pp.ke->fix(&A, 8, stream); });
+    } else if (p->pairs) {
+      tf::PassArgs<tf::dd> A;  // no checksums: no correction kernel
+      fill_args<tf::dd>(p, pi, pin, pout, batch, tbase, inj, A);
+      timed(2 * pi, [&] { pp.ke->main[0](&A, grid, stream); });
     } else {
       tf::PassArgs<double> A;
       fill_args<double>(p, pi, pin, pout, batch, tbase, inj, A);

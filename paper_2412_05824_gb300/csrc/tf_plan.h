@@ -44,7 +44,8 @@ struct Registry {
     }
     tf::EntryTableFn fns[] = {tf::entries_f32_sp, tf::entries_f32_col, tf::entries_f32_row,
                               tf::entries_f64_sp, tf::entries_f64_col, tf::entries_f64_row,
-                              tf::entries_f32_alt_sp, tf::entries_f32_alt_cr, tf::entries_f64_alt};
+                              tf::entries_f32_alt_sp, tf::entries_f32_alt_cr, tf::entries_f64_alt,
+                              tf::entries_pairs};
     for (auto fn : fns) {
       int n = 0;
       const KernelEntry* t = fn(&n);
@@ -110,8 +111,14 @@ template <typename R> std::vector<typename DevC<R>::t> round_table(const std::ve
 
 // default threshold factor gamma per working precision: chosen from clean-run
 // residuals so that the largest clean |S1| stays far below tau
-constexpr double kGamma[2] = {8.0, 16.0};
-constexpr double kUnitRoundoff[2] = {0x1p-24, 0x1p-53};
+// (index: 0 float32, 1 float64, 2 float64 data in float-pair arithmetic,
+// which has no checksums)
+constexpr double kGamma[3] = {8.0, 16.0, 16.0};
+constexpr double kUnitRoundoff[3] = {0x1p-24, 0x1p-53, 0x1p-47};
+// thread-level checks test one transform at a time: the rounding residual of
+// a single transform has a heavier tail relative to its energy than that of
+// a group's sum, so their threshold takes twice the group's gamma
+constexpr double kThreadLevelGammaFactor = 2.0;
 // float32 sizes from 2^this use three passes by default
 constexpr int kThreePassLog2F32 = 22;
 
@@ -149,6 +156,7 @@ struct PassPlan {
 struct turbofft_plan {
   int64_t n = 0, batch = 0;
   int dtype = 0, direction = -1, ft_mode = 0;
+  bool pairs = false;  // float64 data transformed in float-pair arithmetic
   int device = 0;
   int num_passes = 1;
   int n1 = 0, n2 = 1;
@@ -213,13 +221,16 @@ bool upload(turbofft_plan* p, void** dst, const std::vector<cld>& v) {
   if (!dev_alloc(p, dst, bytes)) return false;
   return cudaMemcpy(*dst, t.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess;
 }
+// a table as float pairs (hi, lo) per component, for float-pair plans
+bool upload_pairs(turbofft_plan* p, void** dst, const std::vector<cld>& v);
 bool upload_tables(turbofft_plan* p, PassPlan& pp);
 bool col_tables(turbofft_plan* p, PassPlan& pp, const void* tlo, const void* thi, bool weights);
 
 // ---------------------------------------------------------------------------
 // launches (tf_launch.cu)
 // ---------------------------------------------------------------------------
-int ft_variant(int ft_mode);   // 0 none, 1 checksums, 2 checksums + register sums
+int ft_variant(int ft_mode);   // 0 none, 1 checksums, 2 checksums + register sums, 3 thread-level
+int kernel_dtype(const turbofft_plan* p);  // registry dtype: 0 float32, 1 float64, 2 float pairs
 int cl_variant(int ft_mode);   // cluster kernels: 0 none, 1 checksums
 int occupancy_blocks(const KernelEntry* ke, int variant);
 bool set_smem_attrs(const KernelEntry* ke);

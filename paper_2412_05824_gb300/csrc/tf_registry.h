@@ -8,7 +8,7 @@ namespace tf {
 typedef void (*LaunchFn)(const void* args, int grid, cudaStream_t stream);
 
 struct KernelEntry {
-  int dtype;        // 0 float, 1 double
+  int dtype;        // 0 float, 1 double, 2 double data in float-pair arithmetic
   int kind;         // Kind
   int ns;           // sub-transform length
   int e;            // complex values per thread (= radix of the first passes)
@@ -56,5 +56,7 @@ const KernelEntry* entries_f64_row(int* count);
 const KernelEntry* entries_f32_alt_sp(int* count);
 const KernelEntry* entries_f32_alt_cr(int* count);
 const KernelEntry* entries_f64_alt(int* count);
+// float64 data in float-pair arithmetic (no checksum variants)
+const KernelEntry* entries_pairs(int* count);
 
 }  // namespace tf

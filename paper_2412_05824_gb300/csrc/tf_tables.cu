@@ -93,10 +93,25 @@ bool dev_alloc(turbofft_plan* p, void** ptr, size_t bytes) {
   return true;
 }
 
+bool upload_pairs(turbofft_plan* p, void** dst, const std::vector<cld>& v) {
+  // each component as hi = nearest float, lo = nearest float of the rest
+  // (the long-double value rounded once into 48 significand bits)
+  std::vector<float4> t(v.size());
+  for (size_t i = 0; i < v.size(); ++i) {
+    const ld re = v[i].real(), im = v[i].imag();
+    const float rh = (float)re, ih = (float)im;
+    t[i] = make_float4(rh, (float)(re - (ld)rh), ih, (float)(im - (ld)ih));
+  }
+  const size_t bytes = t.size() * sizeof(float4);
+  if (!dev_alloc(p, dst, bytes)) return false;
+  return cudaMemcpy(*dst, t.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
 bool upload_tables(turbofft_plan* p, PassPlan& pp) {
   const int ns = pp.ns;
   std::vector<cld> tw(ns);
   for (int q = 0; q < ns; ++q) tw[q] = root(ns, q);
+  if (p->pairs) return upload_pairs(p, &pp.d_tw, tw);  // no checksums
   std::vector<cld> e = encoding_vector(ns);
   std::vector<cld> v = e;
   host_fft(v);  // v = W e = (e^T W)^T, W symmetric (Eq. 1)

@@ -84,11 +84,21 @@ def test_null_handles_are_rejected_by_the_other_calls(L):
     assert L.turbofft_last_error(None) == b""
 
 
-@pytest.mark.parametrize("structure", [-1, 4, 99])
+@pytest.mark.parametrize("structure", [-1, 0, 5, 99])
 def test_structured_create_rejects_unknown_structures(L, structure):
     h = ctypes.c_void_p(123)
     st = L.turbofft_plan_create_structured(1 << 14, 4, 0, -1, 0, structure, ctypes.byref(h))
     assert st == tfl.INVALID_VALUE
+    assert not h.value
+
+
+@pytest.mark.parametrize("dtype,ft", [(0, 0), (1, 1), (1, 2), (1, 3), (1, 4)])
+def test_float_pairs_only_for_plain_float64(L, dtype, ft):
+    # float-pair arithmetic: complex128 without checksums only (decided
+    # before any device call)
+    h = ctypes.c_void_p(123)
+    st = L.turbofft_plan_create_structured(1024, 4, dtype, -1, ft, 4, ctypes.byref(h))
+    assert st == tfl.UNSUPPORTED
     assert not h.value
 
 
