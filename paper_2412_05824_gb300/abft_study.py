@@ -132,7 +132,8 @@ def ablation(n: int, dtype: str = "complex64", elements: int = 1 << 26, groups=(
     rows = []
     if thread_level:
         # thread-level ABFT (Sec. 4.2.1) where one thread holds a whole
-        # transform; its plain baseline is the same one-thread shape
+        # transform (its own one-thread shape), against the same plain
+        # baseline as the block-level rows: the default plain shape
         try:
             tl = tfl.Plan(n, batch, dtype, "forward", "correct_thread")
         except tfl.TurboFFTError:

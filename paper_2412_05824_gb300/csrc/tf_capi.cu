@@ -270,7 +270,7 @@ turbofft_status create_plan(int64_t n, int64_t batch, turbofft_dtype dtype, int 
       ok = (dt == 0)   ? (upload<float>(p, lo_dst, lo) && upload<float>(p, hi_dst, hi))
            : (dt == 2) ? (upload_pairs(p, lo_dst, lo) && upload_pairs(p, hi_dst, hi))
                        : (upload<double>(p, lo_dst, lo) && upload<double>(p, hi_dst, hi));
-      if (ok && dt == 1 && !p->cl) ok = col_tables(p, p->pass[pi], *lo_dst, *hi_dst, ft_mode != TURBOFFT_FT_OFF);
+      if (ok && dt == 1 && !p->cl) ok = col_tables(p, p->pass[pi], ft_mode != TURBOFFT_FT_OFF);
     }
     p->scratch_bytes = p->cl ? 0 : (size_t)(batch * n) * elem_bytes(dtype);
     if (!ok) {

@@ -471,16 +471,34 @@ template <class K> __device__ __forceinline__ long long row_unit_first(const Geo
   return t * g.outer + (long long)kb * K::S;
 }
 
+// Column-pass unit -> (transform b, first column c0).  float64 column passes
+// walk the transforms fastest, so that the blocks running at once share their
+// column block and the per-column tables in access order (twiddles, checksum
+// weights) are read from HBM about once per column block, not per transform;
+// float32 column passes (no such tables) walk the columns of a transform.
+template <class K>
+__device__ __forceinline__ void col_unit(const Geo& g, long long unit, long long& b, int& c0) {
+  if constexpr (std::is_same<typename K::real, double>::value) {
+    const long long cb = unit / g.batch;
+    b = unit - cb * g.batch;
+    c0 = (int)cb * K::S;
+  } else {
+    const int blocks = g.n2 / K::S;
+    b = unit / blocks;
+    c0 = (int)(unit - b * blocks) * K::S;
+  }
+}
+
 // signal id of slot `slot` of work unit `unit`; -1 if past the end (ragged tail)
 template <class K> __device__ __forceinline__ long long signal_of(const Geo& g, long long unit, int slot) {
   if constexpr (K::KIND == KIND_SP) {
     long long s = unit * K::S + slot;
     return s < g.batch ? s : -1;
   } else if constexpr (K::KIND == KIND_COL) {
-    const int blocks = g.n2 / K::S;
-    long long b = unit / blocks;
-    int n2 = (int)(unit - b * blocks) * K::S + slot;
-    return b * g.n2 + n2;
+    long long b;
+    int c0;
+    col_unit<K>(g, unit, b, c0);
+    return b * g.n2 + c0 + slot;
   } else {
     if (g.outer > 1) {
       // last pass of a three-pass plan: the S rows of a unit are row k2 of
@@ -817,9 +835,9 @@ __device__ __forceinline__ void issue_unit(const PassArgs<typename K::real>& A, 
       cp_async16(stage + (size_t)sl * K::NS * sizeof(c) + 16 * StageSwz<K>::chunk(sl, j), src + 16 * (size_t)q);
     }
   } else {
-    const int blocks = g.n2 / K::S;
-    const long long b = unit / blocks;
-    const int c0 = (int)(unit - b * blocks) * K::S;
+    long long b;
+    int c0;
+    col_unit<K>(g, unit, b, c0);
     constexpr int cpr = K::S * (int)sizeof(c) / 16;  // 16-byte chunks per row of the tile
     static_assert(cpr >= 1, "a column tile row must span 16 bytes");
     const c* base = A.in + tr_base(g.in_tab, b, g.n) + c0;

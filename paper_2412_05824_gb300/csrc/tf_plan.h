@@ -224,7 +224,7 @@ bool upload(turbofft_plan* p, void** dst, const std::vector<cld>& v) {
 // a table as float pairs (hi, lo) per component, for float-pair plans
 bool upload_pairs(turbofft_plan* p, void** dst, const std::vector<cld>& v);
 bool upload_tables(turbofft_plan* p, PassPlan& pp);
-bool col_tables(turbofft_plan* p, PassPlan& pp, const void* tlo, const void* thi, bool weights);
+bool col_tables(turbofft_plan* p, PassPlan& pp, bool weights);  // float64 column-pass tables, host-built
 
 // ---------------------------------------------------------------------------
 // launches (tf_launch.cu)

@@ -5,6 +5,9 @@
 // kernel registry; plan-owned device allocations.
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <cmath>
+#include <vector>
 #include <stdint.h>
 #include <string.h>
 
@@ -136,48 +139,87 @@ bool upload_tables(turbofft_plan* p, PassPlan& pp) {
 }
 
 namespace {
-// Inter-pass twiddles of a float64 column pass over length L = n1 * n2 in
-// the pass's access order: colw[n2 * n1 + k1] = w_L^{k1 n2}, the same
-// product of the two small tables that float32 column passes form per value,
-// and colwe = e_k1 conj(colw), the output-side checksum weight of a value
-// taken after its twiddle.
-__global__ void col_fill_kernel(double2* colw, double2* colwe, const double2* tlo, const double2* thi,
-                                const double2* ev, int n1, long long total) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long n2 = i / n1;
-    const int k1 = (int)(i - n2 * n1);
-    const unsigned q = (unsigned)k1 * (unsigned)n2;
-    const double2 a = thi[q >> 12], b = tlo[q & 4095u];
-    const double2 w = make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-    colw[i] = w;
-    if (colwe) {
-      const double2 e = ev[k1];
-      colwe[i] = make_double2(e.x * w.x + e.y * w.y, e.y * w.x - e.x * w.y);
-    }
-  }
+// Double-double arithmetic on the host (Dekker / Knuth error-free
+// transformations with FMA): about 106 significand bits, so that a product
+// of two tables rounds once to float64.
+struct D2 {
+  double hi, lo;
+};
+D2 d2_of(ld v) {
+  const double h = (double)v;
+  return {h, (double)(v - (ld)h)};
 }
+D2 d2_add(D2 a, D2 b) {
+  const double s = a.hi + b.hi;
+  const double bb = s - a.hi;
+  const double e = (a.hi - (s - bb)) + (b.hi - bb) + (a.lo + b.lo);
+  const double h = s + e;
+  return {h, e - (h - s)};
+}
+D2 d2_mul(D2 a, D2 b) {
+  const double p = a.hi * b.hi;
+  const double e = std::fma(a.hi, b.hi, -p) + (a.hi * b.lo + a.lo * b.hi);
+  const double h = p + e;
+  return {h, e - (h - p)};
+}
+D2 d2_neg(D2 a) { return {-a.hi, -a.lo}; }
+double d2_round(D2 a) { return a.hi + a.lo; }
 }  // namespace
 
-bool col_tables(turbofft_plan* p, PassPlan& pp, const void* tlo, const void* thi, bool weights) {
-  const long long total = (long long)pp.g_n1 * pp.g_n2;
-  const size_t bytes = (size_t)total * sizeof(double2);
-  if (!dev_alloc(p, &pp.d_colw, bytes)) return false;
-  if (weights && !dev_alloc(p, &pp.d_colwe, bytes)) return false;
-  cudaStream_t st = nullptr;
-  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
+// Inter-pass twiddles of a float64 column pass over length L = n1 * n2 in
+// the pass's access order, computed on the host: colw[n2 * n1 + k1] =
+// w_L^{k1 n2}, and colwe = e_k1 conj(colw), the output-side checksum weight
+// of a value taken after its twiddle.  w_L^q = w_L^{4096 (q >> 12)} *
+// w_L^{q & 4095} from two long-double tables, multiplied in double-double
+// and rounded once to float64 (error below 0.5 ulp + 2^-100).
+bool col_tables(turbofft_plan* p, PassPlan& pp, bool weights) {
+  const int n1 = pp.g_n1;
+  const long long L = (long long)pp.g_n1 * pp.g_n2;
+  const size_t total = (size_t)L;
+  std::vector<D2> lo_re(4096), lo_im(4096), hi_re((size_t)std::max<long long>(1, L / 4096)),
+      hi_im(hi_re.size());
+  for (int j = 0; j < 4096; ++j) {
+    const cld w = root(L, j);
+    lo_re[j] = d2_of(w.real());
+    lo_im[j] = d2_of(w.imag());
   }
-  const int threads = 256;
-  const long long want = (total + threads - 1) / threads;
-  const int blocks = (int)(want < 8192 ? want : 8192);
-  col_fill_kernel<<<blocks, threads, 0, st>>>(static_cast<double2*>(pp.d_colw), static_cast<double2*>(pp.d_colwe),
-                                              static_cast<const double2*>(tlo), static_cast<const double2*>(thi),
-                                              static_cast<const double2*>(pp.d_ev), pp.g_n1, total);
-  const bool ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
-  cudaStreamDestroy(st);
-  return ok;
+  for (size_t j = 0; j < hi_re.size(); ++j) {
+    const cld w = root(L, (int64_t)j * 4096);
+    hi_re[j] = d2_of(w.real());
+    hi_im[j] = d2_of(w.imag());
+  }
+  std::vector<D2> e_re(n1), e_im(n1);
+  if (weights) {
+    const std::vector<cld> e = encoding_vector(n1);
+    for (int k = 0; k < n1; ++k) {
+      e_re[k] = d2_of(e[k].real());
+      e_im[k] = d2_of(e[k].imag());
+    }
+  }
+  std::vector<double2> w_tab(total), we_tab(weights ? total : 0);
+  for (size_t i = 0; i < total; ++i) {
+    const long long n2 = (long long)(i / (size_t)n1);
+    const int k1 = (int)(i - (size_t)n2 * n1);
+    const unsigned q = (unsigned)((long long)k1 * n2 % L);
+    const size_t a = q >> 12, b = q & 4095u;
+    const D2 wr = d2_add(d2_mul(hi_re[a], lo_re[b]), d2_neg(d2_mul(hi_im[a], lo_im[b])));
+    const D2 wi = d2_add(d2_mul(hi_re[a], lo_im[b]), d2_mul(hi_im[a], lo_re[b]));
+    w_tab[i] = make_double2(d2_round(wr), d2_round(wi));
+    if (weights) {
+      // e * conj(w) = (er wr + ei wi) + i (ei wr - er wi)
+      const D2 cr = d2_add(d2_mul(e_re[k1], wr), d2_mul(e_im[k1], wi));
+      const D2 ci = d2_add(d2_mul(e_im[k1], wr), d2_neg(d2_mul(e_re[k1], wi)));
+      we_tab[i] = make_double2(d2_round(cr), d2_round(ci));
+    }
+  }
+  const size_t bytes = total * sizeof(double2);
+  if (!dev_alloc(p, &pp.d_colw, bytes) ||
+      cudaMemcpy(pp.d_colw, w_tab.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+    return false;
+  if (weights && (!dev_alloc(p, &pp.d_colwe, bytes) ||
+                  cudaMemcpy(pp.d_colwe, we_tab.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess))
+    return false;
+  return true;
 }
 
 }  // namespace tfh

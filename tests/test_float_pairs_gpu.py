@@ -28,6 +28,8 @@ def run(x, direction="forward"):
 def expected(x, direction):
     if direction == "forward":
         return oracle.fft(x)
+    if direction == "forward_scaled":
+        return oracle.fft(x) / x.shape[1]
     return oracle.fft(x, inverse=True, scaled=(direction == "inverse"))
 
 
