@@ -282,13 +282,20 @@ def bench_ragged(args, dev, stream, rank, peaks):
     offsets, extent = ss.ragged_offsets(sizes)
     x = ss.uniform_complex_torch(rank_seed(rank) + 100, 1, extent, "float32", device=dev).view(-1)
     y = torch.empty_like(x)
-    tfl.set_autotune(True)
-    t0 = time.perf_counter()
+    # one launch of the persistent ragged kernel (the default), and the graph
+    # of per-size kernels with autotuned shapes
     rag = {"correct": tfl.RaggedPlan(sizes, offsets, "complex64", "forward", "correct"),
            "off": tfl.RaggedPlan(sizes, offsets, "complex64", "forward", "off")}
-    tune_s = time.perf_counter() - t0
-    tfl.set_autotune(False)
-    rag_default = tfl.RaggedPlan(sizes, offsets, "complex64", "forward", "correct")
+    tfl.set_ragged_single_launch(False)
+    tfl.set_autotune(True)
+    t0 = time.perf_counter()
+    try:
+        rag_graph = {"correct": tfl.RaggedPlan(sizes, offsets, "complex64", "forward", "correct"),
+                     "off": tfl.RaggedPlan(sizes, offsets, "complex64", "forward", "off")}
+    finally:
+        tune_s = time.perf_counter() - t0
+        tfl.set_autotune(False)
+        tfl.set_ragged_single_launch(True)
 
     # the same transforms, contiguous per size (gathered once on the device)
     order = np.argsort(sizes, kind="stable")
@@ -322,7 +329,8 @@ def bench_ragged(args, dev, stream, rank, peaks):
     reps = max(args.steps, 5)
     ms = {"ragged_ft": time_calls(run_rag(rag["correct"]), args.warmup, reps, stream),
           "ragged_plain": time_calls(run_rag(rag["off"]), args.warmup, reps, stream),
-          "ragged_ft_default_shapes": time_calls(run_rag(rag_default), args.warmup, reps, stream),
+          "ragged_ft_graph_autotuned": time_calls(run_rag(rag_graph["correct"]), args.warmup, reps, stream),
+          "ragged_plain_graph_autotuned": time_calls(run_rag(rag_graph["off"]), args.warmup, reps, stream),
           "per_size_plain": time_calls(lambda: run_per("off"), args.warmup, reps, stream),
           "per_size_ft": time_calls(lambda: run_per("correct"), args.warmup, reps, stream)}
     rep_ft = rag["correct"].report()
@@ -332,7 +340,8 @@ def bench_ragged(args, dev, stream, rank, peaks):
     torch.cuda.synchronize()
     diff = float(torch.linalg.vector_norm(y[idx] - ys) / torch.linalg.vector_norm(ys))
     nbytes = 16.0 * extent
-    members = rag["correct"].members()
+    members = rag_graph["correct"].members()
+    single = rag["correct"].info()["single_launch"] == 1
     out = {"workload": "%d complex64 forward transforms, sizes 2^%d..2^%d log-uniform (seed %d), packed, "
                        "uniform[-1,1) data" % (RAGGED_COUNT, RAGGED_LOG_LO, RAGGED_LOG_HI, RAGGED_SEED),
            "elements": extent, "bytes_per_exec": nbytes, "reps": reps,
@@ -341,14 +350,17 @@ def bench_ragged(args, dev, stream, rank, peaks):
            "hbm_frac_ragged_ft": round(nbytes / (ms["ragged_ft"] * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
            "abft_overhead_pct": round(100.0 * (ms["ragged_ft"] / ms["ragged_plain"] - 1.0), 2),
            "vs_per_size_plain": round(ms["per_size_plain"] / ms["ragged_ft"], 4),
-           "autotune_s": round(tune_s, 2),
+           "plain_vs_per_size_plain": round(ms["per_size_plain"] / ms["ragged_plain"], 4),
+           "single_launch": single,
+           "graph_autotune_s": round(tune_s, 2),
            "shapes": [[m["n"], m["batch"], m["radix"][0], m["block"][0], m["per_block"][0]] for m in members],
            "shapes_columns": ["n", "count", "radix_pass0", "threads_pass0", "per_block_pass0"],
            "graph_launches_per_exec": 1,
-           "kernel_launches_per_exec": sum(2 * m["num_passes"] for m in members),
+           "kernel_launches_per_exec": 1 if single else sum(2 * m["num_passes"] for m in members),
+           "kernel_launches_per_exec_graph_form": sum(2 * m["num_passes"] for m in members),
            "rel_l2_vs_per_size_plain": diff,
            "detected_last_exec": rep_ft["detected"]}
-    for pl in list(rag.values()) + [rag_default] + [q for v in per.values() for q, _ in v]:
+    for pl in list(rag.values()) + list(rag_graph.values()) + [q for v in per.values() for q, _ in v]:
         pl.close()
     del x, y, xs, ys, idx
     torch.cuda.empty_cache()

@@ -163,7 +163,8 @@ typedef struct {
   int32_t cluster;          /* > 0: both passes run in ONE kernel whose thread-block clusters of
                                this many blocks share each transform (one HBM round trip);
                                grid/block then describe that kernel */
-  int32_t reserved2;
+  int32_t single_launch;    /* ragged plan: 1 if an exec is one launch of the persistent
+                               ragged kernel, 0 if a graph of per-size kernels */
 } turbofft_plan_info;
 
 /* Duration of one kernel of the last exec (turbofft_set_profiling). */
@@ -243,13 +244,24 @@ turbofft_status turbofft_plan_create_structured(int64_t n, int64_t batch, turbof
  *               2^31 elements
  * The plan holds one member plan per distinct size (turbofft_plan_get_member_info,
  * members in ascending size order) whose kernels address their transforms
- * through a device copy of the offsets.  turbofft_exec on a ragged plan
- * launches ONE CUDA graph on `stream` in which the members' kernels are
- * parallel branches; the graph is captured on the first exec and captured
+ * through a device copy of the offsets.
+ *   - F32 plans whose lengths are all <= 2^16, ft_mode OFF, DETECT or
+ *     CORRECT (info.single_launch = 1, unless turned off with
+ *     turbofft_set_ragged_single_launch): turbofft_exec is ONE launch of a
+ *     persistent kernel (cooperative: all blocks resident) whose blocks take
+ *     work items, largest first, from a queue over every member's passes;
+ *     a grid barrier separates the column passes of lengths >= 8192 from
+ *     their row passes, and the corrections of detected groups run inside
+ *     the same launch.  A barrier that waits more than about a second
+ *     makes the exec fail: turbofft_get_report returns TURBOFFT_TIMEOUT.
+ *   - Otherwise: ONE CUDA graph in which the members' kernels are parallel
+ *     branches.
+ * Either form is captured in a CUDA graph on the first exec and captured
  * again whenever `in` or `out` differ from the last captured pair (a
  * synchronous step: do not exec a ragged plan with new pointers inside a
  * stream capture of your own).  An exec with a site armed by
- * turbofft_inject queues the members' kernels directly instead.  The packed
+ * turbofft_inject runs uncaptured (the single launch carries the site; the
+ * graph form queues the members' kernels directly).  The packed
  * buffers span max(offsets[i] + sizes[i]) elements.  turbofft_get_report
  * sums the members' reports, transform indices are the global ones (i), and
  * turbofft_inject takes the global transform index.  turbofft_exec_host
@@ -281,6 +293,14 @@ turbofft_status turbofft_plan_get_member_info(const turbofft_plan *plan, int32_t
  * the same transform.  Returns SUCCESS.
  */
 turbofft_status turbofft_set_autotune(int enable);
+
+/*
+ * Process-wide: whether ragged plans created afterwards run as one launch of
+ * the persistent ragged kernel where they can (enable = 1, the default) or
+ * as a graph of per-size kernels (0).  A batching facility: the paper tunes
+ * one kernel per length (Sec. 3.3).
+ */
+turbofft_status turbofft_set_ragged_single_launch(int enable);
 
 /*
  * Transform `in` into `out` (both device pointers, see the layout above) on

@@ -77,7 +77,7 @@ class PlanInfo(ctypes.Structure):
                 ("block", ctypes.c_int32 * 3), ("workspace_bytes", ctypes.c_int64),
                 ("scratch_bytes", ctypes.c_int64), ("per_block", ctypes.c_int32 * 3),
                 ("num_members", ctypes.c_int32), ("autotuned", ctypes.c_int32),
-                ("cluster", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+                ("cluster", ctypes.c_int32), ("single_launch", ctypes.c_int32)]
 
 
 class KernelTime(ctypes.Structure):
@@ -91,7 +91,7 @@ EXPORTS = [
     "turbofft_set_workspace", "turbofft_set_profiling", "turbofft_get_kernel_times",
     "turbofft_exec_static_scratch", "turbofft_plan_create_ragged", "turbofft_plan_get_member_info",
     "turbofft_set_autotune", "turbofft_plan_create_structured", "turbofft_set_group_transactions",
-    "turbofft_fma_peak",
+    "turbofft_fma_peak", "turbofft_set_ragged_single_launch",
 ]
 
 _lib = None
@@ -114,6 +114,7 @@ def lib() -> ctypes.CDLL:
                                               ctypes.POINTER(vp)]
     L.turbofft_plan_get_member_info.argtypes = [vp, i32, ctypes.POINTER(PlanInfo)]
     L.turbofft_set_autotune.argtypes = [i32]
+    L.turbofft_set_ragged_single_launch.argtypes = [i32]
     L.turbofft_set_group_transactions.argtypes = [vp, i32]
     L.turbofft_plan_create_structured.argtypes = [i64, i64, i32, i32, i32, i32, ctypes.POINTER(vp)]
     L.turbofft_inject.argtypes = [vp, Site, i32]
@@ -308,6 +309,13 @@ def set_autotune(enable: bool = True):
     """Process-wide: plans created afterwards time their candidate launch
     shapes and keep the fastest (turbofft_set_autotune)."""
     _check(lib().turbofft_set_autotune(1 if enable else 0), "turbofft_set_autotune")
+
+
+def set_ragged_single_launch(enable: bool = True):
+    """Process-wide: ragged plans created afterwards run as one launch of the
+    persistent ragged kernel where they can (default), or as a graph of
+    per-size kernels (turbofft_set_ragged_single_launch)."""
+    _check(lib().turbofft_set_ragged_single_launch(1 if enable else 0), "turbofft_set_ragged_single_launch")
 
 
 def packed_offsets(sizes, dtype="complex64"):

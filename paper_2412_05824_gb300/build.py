@@ -22,6 +22,7 @@ SOURCES = [
     "tf_launch.cu",
     "tf_autotune.cu",
     "tf_ragged.cu",
+    "tf_ragged_kernel.cu",
     "tf_noalloc.cu",
     "tf_peaks.cu",
     "tf_k_f32_sp.cu",

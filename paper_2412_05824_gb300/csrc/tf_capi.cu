@@ -60,6 +60,7 @@ void fill_info(const turbofft_plan* p, turbofft_plan_info* info) {
   info->group_transactions = p->T;
   if (p->ragged) {
     info->num_members = (int32_t)p->members.size();
+    info->single_launch = p->rg ? 1 : 0;
     for (auto m : p->members) {
       info->workspace_bytes += m->workspace_bytes + (m->scratch_owned ? 0 : (int64_t)m->scratch_bytes);
       info->autotuned |= m->autotuned ? 1 : 0;
@@ -170,7 +171,7 @@ turbofft_status create_plan(int64_t n, int64_t batch, turbofft_dtype dtype, int 
     p->pass[1].ns = 1 << b;
     p->pass[2].kind = tf::KIND_ROW;
     p->pass[2].ns = 1 << c;
-  } else if (n <= reg.max_sp(dt)) {
+  } else if (n <= reg.max_sp(dt) && !(structure == 5 && n > 4096)) {
     p->num_passes = 1;
     p->n1 = (int)n;
     p->n2 = 1;
@@ -337,6 +338,7 @@ turbofft_status turbofft_destroy(turbofft_plan* p) {
   cudaDeviceSynchronize();
   for (auto m : p->members) turbofft_destroy(m);
   drop_graph(p);
+  rg_free(p);
   for (auto st : p->branch_streams)
     if (st) cudaStreamDestroy(st);
   for (auto ev : p->branch_events)
@@ -532,6 +534,15 @@ turbofft_status turbofft_get_report(turbofft_plan* p, turbofft_report* r) {
   memset(r, 0, sizeof(*r));
   r->first_transform = -1;
   r->first_pass = -1;
+  if (p->rg && p->have_exec) {
+    // one-launch ragged exec: a grid barrier that gave up waiting
+    cudaError_t e = cudaEventSynchronize(p->done);
+    if (e != cudaSuccess) return cuda_fail(p, e, "report wait");
+    if (rg_timed_out(p)) {
+      p->last_error = "ragged persistent kernel: grid barrier timed out";
+      return TURBOFFT_TIMEOUT;
+    }
+  }
   if (p->ft_mode == TURBOFFT_FT_OFF || !p->have_exec) return TURBOFFT_SUCCESS;
   cudaError_t e = cudaEventSynchronize(p->done);
   if (e != cudaSuccess) return cuda_fail(p, e, "report wait");

@@ -863,9 +863,15 @@ __device__ __forceinline__ void atomic_max_nonneg(float* addr, float v) {
 // (Sec. 4.2.1): every thread checks its own whole transform against a
 // per-transform threshold, with no block reduction; a failing transform is
 // recorded for the correction kernel, which recomputes it
+//
+// pass_body: the block's share of a pass, the work units first, first +
+// stride, ... below end (the pass kernel: blockIdx.x, gridDim.x, all units;
+// the persistent ragged kernel: a contiguous range per work item).  The
+// caller makes sure that no thread of the block still uses shared memory of
+// an earlier call.
 template <class K, int FTM>
-__global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_FT : TwMode<K>::MINB)
-    tf_pass_kernel(const PassArgs<typename K::real> A) {
+__device__ __forceinline__ void pass_body(const PassArgs<typename K::real>& A, char* smem_raw, long long first,
+                                          long long stride, long long end) {
   using R = typename K::real;
   using c = typename K::c;
   constexpr int E = K::E, P = K::P, S = K::S;
@@ -873,14 +879,11 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
   constexpr bool EAGER = FTM == 2;
   constexpr bool TL = FTM == 3;
   static_assert(!TL || thread_level_ok<K>(), "thread-level checksums need one thread per transform");
-  extern __shared__ __align__(128) unsigned char smem_raw_[];
-  char* smem_raw = reinterpret_cast<char*>(smem_raw_);
 
   const int tid = threadIdx.x;
   const int slot = K::SLOT_FAST ? (tid % S) : (tid / P);
   const int t = K::SLOT_FAST ? (tid / S) : (tid % P);
   const Geo g = A.geo;
-  const long long stride = gridDim.x;
   TwReg<K, FT ? TF_FT_TW_BUDGET : 64> twr;
   twr.load(A.tw, t);
   const unsigned long long mask_in = sign_mask<c>(A.conj_in), mask_out = sign_mask<c>(A.conj_out);
@@ -919,7 +922,7 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
   int bad_lo = 0x7fffffff, bad_hi = -1;
   unsigned checked = 0;           // transforms checked (thread-level mode)
   int gi = 0;                     // transaction index inside the group
-  long long g_unit0 = blockIdx.x;
+  long long g_unit0 = first;
   long long groups = 0;
   float max_ratio2 = 0.f;  // max (|S1| / tau)^2 over clean groups
   const R tau_coef2 = (R)(A.tau_coef * A.tau_coef);
@@ -931,17 +934,17 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
   // prologue: the first NSTAGE-1 transactions' tiles in flight
 #pragma unroll
   for (int k = 0; k < NSTAGE - 1; ++k) {
-    const long long u = blockIdx.x + k * stride;
-    if (u < A.num_units) issue_unit<K>(A, u, smem_raw + k * stage_bytes<K>(), tid);
+    const long long u = first + k * stride;
+    if (u < end) issue_unit<K>(A, u, smem_raw + k * stage_bytes<K>(), tid);
     cp_async_commit();
   }
   int it = 0;
-  for (long long unit = blockIdx.x; unit < A.num_units; unit += stride, ++it) {
+  for (long long unit = first; unit < end; unit += stride, ++it) {
     // prefetch NSTAGE-1 transactions ahead into the stage freed by the
     // previous transaction, then wait for this transaction's tile
     {
       const long long un = unit + (NSTAGE - 1) * stride;
-      if (un < A.num_units) issue_unit<K>(A, un, smem_raw + ((it + NSTAGE - 1) % NSTAGE) * stage_bytes<K>(), tid);
+      if (un < end) issue_unit<K>(A, un, smem_raw + ((it + NSTAGE - 1) % NSTAGE) * stage_bytes<K>(), tid);
       cp_async_commit();
       cp_async_wait<NSTAGE - 1>();
       __syncthreads();
@@ -1196,7 +1199,7 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
       s2i += (R)(gi + 1) * ri;
     }
     ++gi;
-    const bool group_end = (gi == A.T) || (unit + stride >= A.num_units);
+    const bool group_end = (gi == A.T) || (unit + stride >= end);
     if constexpr (FT && !TL) {
       if (group_end) {
         // ---- reduce the group over the threads of each slot.  Phase 1
@@ -1347,6 +1350,13 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
   }
 }
 
+template <class K, int FTM>
+__global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_FT : TwMode<K>::MINB)
+    tf_pass_kernel(const PassArgs<typename K::real> A) {
+  extern __shared__ __align__(128) unsigned char smem_raw_[];
+  pass_body<K, FTM>(A, reinterpret_cast<char*>(smem_raw_), blockIdx.x, gridDim.x, A.num_units);
+}
+
 // ---------------------------------------------------------------------------
 // correction kernel: one block per record of this pass (Sec. 4.1.2)
 //   located signal k:  Delta = y_bar - W x_bar,  y_k <- y_k - Delta, re-check;
@@ -1360,7 +1370,7 @@ __device__ __forceinline__ void load_input(const PassArgs<typename K::real>& A, 
                                            typename K::c (&a)[K::E]) {
 #pragma unroll
   for (int i = 0; i < K::E; ++i) {
-    auto v = A.in[in_off<K>(A.geo, sig, t + i * K::P)];
+    auto v = __ldcg(A.in + in_off<K>(A.geo, sig, t + i * K::P));  // L2: other blocks' writes are visible
     a[i] = A.conj_in ? cconj(v) : v;
   }
 }
@@ -1374,7 +1384,7 @@ __device__ __forceinline__ void load_output_internal(const PassArgs<typename K::
 #pragma unroll
   for (int i = 0; i < K::E; ++i) {
     const int pos = t + i * K::P;
-    auto v = A.out[out_off<K>(A.geo, sig, pos)];
+    auto v = __ldcg(A.out + out_off<K>(A.geo, sig, pos));
     v = cscale(v, (R)1 / A.out_scale);
     if (A.conj_out) v = cconj(v);
     if constexpr (K::KIND == KIND_COL) v = cmul(v, cconj(col_w<K>(A, sig, pos)));
@@ -1446,21 +1456,26 @@ __device__ __forceinline__ bool signal_passes(const PassArgs<typename K::real>& 
   return m <= A.tau_coef * sqrt((double)K::NS * en);  // false for NaN
 }
 
+// fix_body: records first, first + stride, ... of this pass (the correction
+// kernel: blockIdx.x, gridDim.x; the persistent ragged kernel after a grid
+// barrier).  `red` is block-shared scratch of 3 x 32 doubles.
 template <class K>
-__global__ void __launch_bounds__(K::NT) tf_fix_kernel(const PassArgs<typename K::real> A) {
+__device__ __forceinline__ void fix_body(const PassArgs<typename K::real>& A, char* smem_raw, double* red,
+                                         unsigned long long first, unsigned long long stride) {
   using c = typename K::c;
   constexpr int E = K::E, P = K::P, S = K::S;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   c* sm = reinterpret_cast<c*>(smem_raw);
-  __shared__ double red[3 * 32];
 
-  const unsigned long long nrec = A.fts->num_records;
+  // the records and their count are read around L1 (volatile): in the
+  // persistent ragged kernel other blocks wrote them after this block may
+  // have cached the lines
+  const unsigned long long nrec = *reinterpret_cast<volatile unsigned long long*>(&A.fts->num_records);
   const int tid = threadIdx.x;
   const int slot = K::SLOT_FAST ? (tid % S) : (tid / P);
   const int t = K::SLOT_FAST ? (tid / S) : (tid % P);
 
-  for (unsigned long long r = blockIdx.x; r < nrec && r < (unsigned long long)MAX_RECORDS; r += gridDim.x) {
-    FtRecord& rec = A.fts->rec[r];
+  for (unsigned long long r = first; r < nrec && r < (unsigned long long)MAX_RECORDS; r += stride) {
+    volatile FtRecord& rec = A.fts->rec[r];
     // uniform across the block: records of other passes, or already handled
     if (rec.pass_id != A.pass_id || rec.result != FT_RES_PENDING) continue;
     auto sig_of = [&](int k) { return signal_of<K>(A.geo, rec.unit0 + (long long)k * rec.unit_stride, rec.slot); };
@@ -1582,6 +1597,13 @@ __global__ void __launch_bounds__(K::NT) tf_fix_kernel(const PassArgs<typename K
     }
     __syncthreads();
   }
+}
+
+template <class K>
+__global__ void __launch_bounds__(K::NT) tf_fix_kernel(const PassArgs<typename K::real> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[3 * 32];
+  fix_body<K>(A, reinterpret_cast<char*>(smem_raw), red, blockIdx.x, gridDim.x);
 }
 
 }  // namespace tf

@@ -20,6 +20,7 @@
 #include "tf_device.cuh"
 #include "tf_internal.h"
 #include "tf_plan.h"
+#include "tf_ragged_kernel.h"
 
 namespace tfh {
 
@@ -118,6 +119,15 @@ void fill_args(const turbofft_plan* p, int pi, const void* in, void* out, int64_
   A.rec_stride = p->rec_stride;
   A.inj = inj;
 }
+
+}  // namespace
+
+void fill_pass_args_f32(const turbofft_plan* p, int pi, const void* in, void* out, const tf::InjectSite& inj,
+                        tf::PassArgs<float>* A) {
+  fill_args<float>(p, pi, in, out, p->batch, 0, inj, *A);
+}
+
+namespace {
 
 template <typename R>
 void fill_cl_args(const turbofft_plan* p, const void* in, void* out, int64_t batch, int64_t tbase,

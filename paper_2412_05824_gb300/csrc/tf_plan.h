@@ -198,6 +198,7 @@ struct turbofft_plan {
   const void* graph_in = nullptr;
   void* graph_out = nullptr;
   bool armed_any = false;
+  void* rg = nullptr;               // ragged: state of the one-launch persistent kernel, if used
   std::vector<int32_t> member_of;  // ragged: member plan of each global transform
   std::vector<int64_t> local_of;   // ragged: index of each global transform within its member
   bool autotuned = false;          // launch shapes chosen by timing (turbofft_set_autotune)
@@ -263,12 +264,16 @@ double time_with_temp(turbofft_plan* p);
 // ---------------------------------------------------------------------------
 void drop_graph(turbofft_plan* p);
 turbofft_status exec_ragged(turbofft_plan* p, const void* in, void* out, cudaStream_t s);
+extern std::atomic<int> g_ragged_single;  // new ragged plans use the persistent kernel where they can
+void rg_free(turbofft_plan* p);
+bool rg_timed_out(const turbofft_plan* p);  // the last exec's grid barrier gave up waiting
 
 // ---------------------------------------------------------------------------
 // plans, reports (tf_capi.cu)
 // ---------------------------------------------------------------------------
 // structure: 0 = default, 1 = single pass or two passes, 2 = cluster single
-// pass, 3 = three passes
+// pass, 3 = three passes, 4 = float pairs, 5 = as 1 with one pass only up to
+// 4096 (members of a ragged plan run by the persistent kernel)
 turbofft_status create_plan(int64_t n, int64_t batch, turbofft_dtype dtype, int direction, turbofft_ft_mode ft_mode,
                             int structure, turbofft_plan** out);
 void add_report(const turbofft_plan* m, const std::vector<int64_t>* ids, turbofft_report* r);

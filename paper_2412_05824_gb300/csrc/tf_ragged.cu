@@ -1,6 +1,10 @@
 // Ragged batches: one member plan per distinct size addressing its
-// transforms through a device offset table, run as the parallel branches of
-// one CUDA graph captured per (in, out) pair.
+// transforms through a device offset table.  A float32 batch of lengths
+// 8 .. 2^16 runs as ONE launch of the persistent ragged kernel
+// (tf_ragged_kernel.cu) over a size-sorted work queue; other batches (and
+// plans created with the single launch switched off) run the members as the
+// parallel branches of one CUDA graph.  Either form is captured per
+// (in, out) pair.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -17,15 +21,229 @@
 #include <vector>
 
 #include "tf_plan.h"
+#include "tf_ragged_kernel.h"
 
 namespace tfh {
+
+std::atomic<int> g_ragged_single{1};
+
+// state of a ragged plan run by the persistent kernel
+struct RgState {
+  std::vector<int> ca_member, ca_pass, ca_cls, ca_phase;  // pass entries
+  std::vector<long long> ca_units;
+  tf::RgItem* d_items[2] = {nullptr, nullptr};
+  long long num_items[2] = {0, 0};
+  int num_phases = 1;
+  int ftm = 0;
+  int grid = 0;
+  size_t smem = 0;
+  tf::RgCtl* d_ctl = nullptr;
+  tf::RgCtl* h_ctl = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  const void* g_in = nullptr;
+  void* g_out = nullptr;
+};
+
+void rg_free(turbofft_plan* p) {
+  RgState* r = static_cast<RgState*>(p->rg);
+  if (!r) return;
+  if (r->graph) cudaGraphExecDestroy(r->graph);
+  for (auto d : r->d_items)
+    if (d) cudaFree(d);
+  if (r->d_ctl) cudaFree(r->d_ctl);
+  if (r->h_ctl) cudaFreeHost(r->h_ctl);
+  if (r->cs) cudaStreamDestroy(r->cs);
+  delete r;
+  p->rg = nullptr;
+}
 
 void drop_graph(turbofft_plan* p) {
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
   p->graph_exec = nullptr;
   p->graph_in = nullptr;
   p->graph_out = nullptr;
+  if (RgState* r = static_cast<RgState*>(p->rg)) {
+    if (r->graph) cudaGraphExecDestroy(r->graph);
+    r->graph = nullptr;
+    r->g_in = nullptr;
+    r->g_out = nullptr;
+  }
 }
+
+bool rg_timed_out(const turbofft_plan* p) {
+  const RgState* r = static_cast<const RgState*>(p->rg);
+  return r && r->h_ctl && r->h_ctl->error != 0;
+}
+
+namespace {
+
+// size class of pass pi of a member of length n (-1: none)
+int rg_class_of(int64_t n, int pi, int num_passes, int n1, int n2) {
+  const tf::RgClassInfo* ci = tf::ragged_classes();
+  const int kind = num_passes == 1 ? tf::KIND_SP : (pi == 0 ? tf::KIND_COL : tf::KIND_ROW);
+  const int ns = num_passes == 1 ? (int)n : (pi == 0 ? n1 : n2);
+  for (int c = 0; c < tf::kRgClasses; ++c)
+    if (ci[c].kind == kind && ci[c].ns == ns) return c;
+  return -1;
+}
+
+// work units of pass entry (member m, pass pi) in class c
+long long rg_units(const turbofft_plan* m, int pi, const tf::RgClassInfo& c) {
+  if (c.kind == tf::KIND_SP) return (m->batch + c.s - 1) / c.s;
+  if (c.kind == tf::KIND_COL) return m->batch * (m->n2 / c.s);
+  return m->batch * (m->n1 / c.s);
+}
+
+// Build the work queue of a ragged plan whose members the persistent kernel
+// can run; false (and no state) otherwise.
+bool rg_setup(turbofft_plan* p) {
+  if (p->dtype != TURBOFFT_C2C_F32) return false;
+  if (p->ft_mode != TURBOFFT_FT_OFF && p->ft_mode != TURBOFFT_FT_DETECT && p->ft_mode != TURBOFFT_FT_CORRECT)
+    return false;
+  const tf::RgClassInfo* ci = tf::ragged_classes();
+  RgState* r = new RgState();
+  r->ftm = p->ft_mode == TURBOFFT_FT_OFF ? 0 : 1;
+  struct Piece {
+    int ca;
+    long long u0, u1;
+    long long bytes;
+  };
+  std::vector<Piece> pieces[2];
+  size_t smem = 0;
+  bool ok = true;
+  for (size_t k = 0; k < p->members.size() && ok; ++k) {
+    const turbofft_plan* m = p->members[k];
+    if (m->cl || m->num_passes > 2 || m->T < 1) ok = false;
+    for (int pi = 0; ok && pi < m->num_passes; ++pi) {
+      const int c = rg_class_of(m->n, pi, m->num_passes, m->n1, m->n2);
+      if (c < 0 || (int)r->ca_cls.size() >= tf::kRgMaxPasses) {
+        ok = false;
+        break;
+      }
+      const int phase = (m->num_passes == 2 && pi == 1) ? 1 : 0;
+      const int ca = (int)r->ca_cls.size();
+      const long long units = rg_units(m, pi, ci[c]);
+      r->ca_member.push_back((int)k);
+      r->ca_pass.push_back(pi);
+      r->ca_cls.push_back(c);
+      r->ca_phase.push_back(phase);
+      r->ca_units.push_back(units);
+      smem = std::max(smem, (size_t)(r->ftm ? std::max(ci[c].smem_ft, ci[c].smem_fix) : ci[c].smem_plain));
+      // items of about 256 KB of input, whole checksum groups of T units
+      const long long ubytes = (long long)ci[c].s * ci[c].ns * 8;
+      long long per = std::max<long long>(1, (256 << 10) / ubytes);
+      per = (per + m->T - 1) / m->T * m->T;
+      for (long long u = 0; u < units; u += per)
+        pieces[phase].push_back({ca, u, std::min(units, u + per), ubytes * (std::min(units, u + per) - u)});
+      if (phase == 1) r->num_phases = 2;
+    }
+  }
+  if (ok) {
+    r->smem = smem;
+    const void* fn = tf::ragged_kernel_fn(r->ftm);
+    int per_sm = 0;
+    ok = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
+         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, tf::kRgThreads, smem) == cudaSuccess &&
+         per_sm >= 1;
+    r->grid = per_sm * g_num_sms;
+  }
+  for (int ph = 0; ok && ph < r->num_phases; ++ph) {
+    // largest items first: the queue's tail holds the small ones
+    std::stable_sort(pieces[ph].begin(), pieces[ph].end(), [&](const Piece& a, const Piece& b) {
+      return ci[r->ca_cls[a.ca]].ns * ci[r->ca_cls[a.ca]].s > ci[r->ca_cls[b.ca]].ns * ci[r->ca_cls[b.ca]].s;
+    });
+    std::vector<tf::RgItem> items(pieces[ph].size());
+    for (size_t i = 0; i < items.size(); ++i) items[i] = tf::RgItem{pieces[ph][i].ca, 0, pieces[ph][i].u0, pieces[ph][i].u1};
+    r->num_items[ph] = (long long)items.size();
+    const size_t bytes = std::max<size_t>(1, items.size()) * sizeof(tf::RgItem);
+    ok = cudaMalloc((void**)&r->d_items[ph], bytes) == cudaSuccess &&
+         cudaMemcpy(r->d_items[ph], items.data(), items.size() * sizeof(tf::RgItem), cudaMemcpyHostToDevice) ==
+             cudaSuccess;
+  }
+  if (ok)
+    ok = cudaMalloc((void**)&r->d_ctl, sizeof(tf::RgCtl)) == cudaSuccess &&
+         cudaHostAlloc((void**)&r->h_ctl, sizeof(tf::RgCtl), cudaHostAllocDefault) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&r->cs, cudaStreamNonBlocking) == cudaSuccess;
+  if (ok) memset(r->h_ctl, 0, sizeof(tf::RgCtl));
+  p->rg = r;
+  if (!ok) {
+    cudaGetLastError();
+    rg_free(p);
+  }
+  return ok;
+}
+
+// one exec on `s`: control block and reports cleared, the kernel, reports
+// and control block copied to their host mirrors
+turbofft_status rg_queue(turbofft_plan* p, const void* in, void* out, cudaStream_t s, bool with_sites) {
+  RgState* r = static_cast<RgState*>(p->rg);
+  tf::RgParams P;
+  memset(&P, 0, sizeof(P));
+  const tf::InjectSite none{};
+  for (size_t i = 0; i < r->ca_cls.size(); ++i) {
+    turbofft_plan* m = p->members[(size_t)r->ca_member[i]];
+    const int pi = r->ca_pass[i];
+    const void* pin = pi == 0 ? in : m->d_scratch;
+    void* pout = (m->num_passes == 2 && pi == 0) ? m->d_scratch : out;
+    fill_pass_args_f32(m, pi, pin, pout, with_sites ? m->armed : none, &P.ca[i].A);
+    P.ca[i].A.num_units = r->ca_units[i];
+    P.ca[i].cls = r->ca_cls[i];
+    P.ca[i].phase = r->ca_phase[i];
+  }
+  P.num_ca = (int)r->ca_cls.size();
+  P.num_phases = r->num_phases;
+  for (int ph = 0; ph < 2; ++ph) {
+    P.num_items[ph] = r->num_items[ph];
+    P.items[ph] = r->d_items[ph];
+  }
+  P.ctl = r->d_ctl;
+  cudaError_t e = cudaMemsetAsync(r->d_ctl, 0, sizeof(tf::RgCtl), s);
+  const bool ft = p->ft_mode != TURBOFFT_FT_OFF;
+  for (size_t k = 0; ft && e == cudaSuccess && k < p->members.size(); ++k)
+    e = cudaMemsetAsync(p->members[k]->d_fts, 0, tf::FT_HEADER_BYTES, s);
+  if (e == cudaSuccess) e = tf::launch_ragged_kernel(r->ftm, P, r->grid, r->smem, s);
+  for (size_t k = 0; ft && e == cudaSuccess && k < p->members.size(); ++k)
+    e = cudaMemcpyAsync(p->members[k]->h_fts, p->members[k]->d_fts, sizeof(FtState), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(r->h_ctl, r->d_ctl, sizeof(tf::RgCtl), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(p, e, "ragged persistent launch");
+  return TURBOFFT_SUCCESS;
+}
+
+turbofft_status rg_exec(turbofft_plan* p, const void* in, void* out, cudaStream_t s) {
+  RgState* r = static_cast<RgState*>(p->rg);
+  if (p->armed_any) {
+    // an armed site: the launch carries it (not the captured graph)
+    p->armed_any = false;
+    turbofft_status st = rg_queue(p, in, out, s, true);
+    for (auto m : p->members) m->armed.active = 0;
+    return st;
+  }
+  if (!r->graph || r->g_in != in || r->g_out != out) {
+    if (r->graph) cudaGraphExecDestroy(r->graph);
+    r->graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(r->cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(p, e, "graph capture");
+    turbofft_status st = rg_queue(p, in, out, r->cs, false);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(r->cs, &g);
+    if (st == TURBOFFT_SUCCESS && e == cudaSuccess) e = cudaGraphInstantiate(&r->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (st != TURBOFFT_SUCCESS) return st;
+    if (e != cudaSuccess) {
+      r->graph = nullptr;
+      return cuda_fail(p, e, "graph capture");
+    }
+    r->g_in = in;
+    r->g_out = out;
+  }
+  cudaError_t e = cudaGraphLaunch(r->graph, s);
+  if (e != cudaSuccess) return cuda_fail(p, e, "graph launch");
+  return TURBOFFT_SUCCESS;
+}
+
+}  // namespace
+
 
 namespace {
 
@@ -77,7 +295,10 @@ turbofft_status exec_ragged(turbofft_plan* p, const void* in, void* out, cudaStr
       if (!dev_alloc(m, &m->d_scratch, m->scratch_bytes)) return TURBOFFT_ALLOC_FAILED;
       m->scratch_owned = true;
     }
-  if (p->armed_any) {
+  if (p->rg) {
+    turbofft_status st = rg_exec(p, in, out, s);
+    if (st != TURBOFFT_SUCCESS) return st;
+  } else if (p->armed_any) {
     // an armed site: queue the members directly (the graph holds no site)
     p->armed_any = false;
     for (auto m : p->members) {
@@ -157,11 +378,17 @@ turbofft_status turbofft_plan_create_ragged(const int64_t* sizes, const int64_t*
   }
   p->member_of.assign((size_t)count, 0);
   p->local_of.assign((size_t)count, 0);
+  // one persistent launch for float32 lengths up to 2^16 (members with one
+  // pass up to 4096, two passes above, as the kernel's size classes)
+  bool single = g_ragged_single.load() != 0 && dtype == TURBOFFT_C2C_F32 &&
+                (ft_mode == TURBOFFT_FT_OFF || ft_mode == TURBOFFT_FT_DETECT || ft_mode == TURBOFFT_FT_CORRECT);
+  for (auto& g : groups) single = single && g.first <= (int64_t)1 << 16;
   t_ragged_member = true;
   turbofft_status st = TURBOFFT_SUCCESS;
   for (auto& g : groups) {
     turbofft_plan* m = nullptr;
-    st = turbofft_plan_create(g.first, (int64_t)g.second.size(), dtype, direction, ft_mode, &m);
+    st = single ? create_plan(g.first, (int64_t)g.second.size(), dtype, direction, ft_mode, 5, &m)
+                : turbofft_plan_create(g.first, (int64_t)g.second.size(), dtype, direction, ft_mode, &m);
     if (st != TURBOFFT_SUCCESS) break;
     p->members.push_back(m);
     p->member_ids.push_back(g.second);
@@ -215,7 +442,13 @@ turbofft_status turbofft_plan_create_ragged(const int64_t* sizes, const int64_t*
     for (void* q : {a, b, c})
       if (q) cudaFree(q);
   }
+  if (single) rg_setup(p);  // else (or if it cannot be set up) the graph of members
   *out = p;
+  return TURBOFFT_SUCCESS;
+}
+
+turbofft_status turbofft_set_ragged_single_launch(int enable) {
+  g_ragged_single.store(enable ? 1 : 0);
   return TURBOFFT_SUCCESS;
 }
 

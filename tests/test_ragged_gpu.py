@@ -1,4 +1,6 @@
-"""Ragged batches of mixed power-of-two sizes (one plan, one CUDA graph).
+"""Ragged batches of mixed power-of-two sizes (one plan; one launch of the
+persistent ragged kernel for float32 lengths up to 2^16, else one CUDA graph
+of per-size kernels).
 
 Parity of every transform of a ragged batch with the CPU oracle (relative L2
 per transform <= 2e-6 log2 N for complex64, 5e-15 log2 N for complex128),
@@ -100,12 +102,17 @@ def test_ragged_matches_oracle(dt, direction, ft):
 
 @pytest.mark.parametrize("ft", ["off", "correct"])
 def test_ragged_equals_per_size_plans_bitwise(ft):
-    """Each member runs the same kernel as the plain plan of its size and
-    count; only the addressing differs, so the bits agree."""
+    """Graph form: each member runs the same kernel as the plain plan of its
+    size and count; only the addressing differs, so the bits agree."""
     tfl.set_autotune(False)
     sizes, offsets, extent = layout(33, 120, 3, 16)
     x = packed_input(8, extent, "c64")
-    plan = tfl.RaggedPlan(sizes, offsets, "complex64", "forward", ft)
+    tfl.set_ragged_single_launch(False)
+    try:
+        plan = tfl.RaggedPlan(sizes, offsets, "complex64", "forward", ft)
+    finally:
+        tfl.set_ragged_single_launch(True)
+    assert plan.info()["single_launch"] == 0
     y = run_ragged(plan, x)
     for n in np.unique(sizes):
         idx = np.nonzero(sizes == n)[0]
@@ -316,3 +323,79 @@ def test_autotune_structure_choice_stays_correct():
         y = p.exec(torch.from_numpy(x).cuda()).cpu().numpy()
         assert float(np.max(oracle.rel_l2(y, oracle.fft(x)))) <= oracle.tolerance(np.float32, n)
         p.close()
+
+
+@pytest.mark.parametrize("ft", ["off", "correct", "detect"])
+@pytest.mark.parametrize("direction", ["forward", "inverse"])
+def test_single_launch_matches_graph_form(ft, direction):
+    """One launch of the persistent kernel against the graph of per-size
+    kernels: bit for bit where both use the same radix (every length but
+    8192, which the single launch runs as two passes 64 x 128), within the
+    bar of the oracle everywhere; gaps untouched; no false alarm."""
+    sizes, offsets, extent = layout(41, 300, 3, 16, max_gap=32)
+    x = packed_input(9, extent, "c64")
+    one = tfl.RaggedPlan(sizes, offsets, "complex64", direction, ft)
+    assert one.info()["single_launch"] == 1
+    tfl.set_ragged_single_launch(False)
+    try:
+        graph = tfl.RaggedPlan(sizes, offsets, "complex64", direction, ft)
+    finally:
+        tfl.set_ragged_single_launch(True)
+    y1 = run_ragged(one, x)
+    y2 = run_ragged(graph, x)
+    check_against_oracle(y1, x, sizes, offsets, "c64", direction)
+    assert np.all(np.isnan(y1[gap_mask(sizes, offsets, extent)].real))
+    for n, o in zip(sizes, offsets):
+        if n != 8192:
+            assert np.array_equal(y1[o:o + n].view(np.uint64), y2[o:o + n].view(np.uint64)), int(n)
+    if ft != "off":
+        rep = one.report()
+        assert rep["detected"] == 0 and rep["status"] == tfl.SUCCESS and rep["groups_checked"] > 0, rep
+    # repeated execs (the captured launch) give the same bits
+    y3 = run_ragged(one, x)
+    assert np.array_equal(np.nan_to_num(y1).view(np.uint64), np.nan_to_num(y3).view(np.uint64))
+    one.close()
+    graph.close()
+
+
+def test_single_launch_injection_and_correction():
+    """Faults injected into a single-launch exec (one seeded bit per exec, in
+    every pass of every length class) are detected on the right global
+    transform and corrected inside the same launch."""
+    sizes, offsets, extent = layout(52, 200, 3, 16)
+    x = packed_input(10, extent, "c64")
+    plan = tfl.RaggedPlan(sizes, offsets, "complex64", "forward", "correct")
+    assert plan.info()["single_launch"] == 1
+    ref = run_ragged(plan, x)
+    members = {m["n"]: m for m in plan.members()}
+    rng = np.random.default_rng(52)
+    seen = set()
+    for tr in rng.permutation(len(sizes))[:40]:
+        n = int(sizes[tr])
+        m = members[n]
+        p = int(rng.integers(0, m["num_passes"]))
+        st = int(rng.integers(0, m["stages"][p] + 1))
+        plan.inject(int(tr), p, st, int(rng.integers(0, n)), int(rng.integers(0, 2)), 30)
+        y = run_ragged(plan, x)
+        rep = plan.report()
+        assert rep["detected"] >= 1 and rep["corrected"] >= 1 and rep["uncorrectable"] == 0, (n, p, st, rep)
+        assert rep["first_transform"] == tr
+        check_against_oracle(y, x, sizes, offsets, "c64")
+        seen.add((n, p))
+    assert len(seen) >= 8
+    # the next exec is clean again (the captured launch holds no site)
+    y = run_ragged(plan, x)
+    assert plan.report()["detected"] == 0
+    assert np.array_equal(y.view(np.uint64), ref.view(np.uint64))
+    plan.close()
+
+
+def test_single_launch_applies_only_where_it_can():
+    sizes, offsets, extent = layout(7, 40, 3, 16)
+    assert tfl.RaggedPlan(sizes, offsets, "complex64", "forward", "off").info()["single_launch"] == 1
+    # float64, the register-sums mode and lengths above 2^16 keep the graph
+    assert tfl.RaggedPlan(sizes, offsets, "complex128", "forward", "off").info()["single_launch"] == 0
+    assert tfl.RaggedPlan(sizes, offsets, "complex64", "forward", "correct_registers").info()["single_launch"] == 0
+    big = list(sizes) + [1 << 17]
+    offs = list(offsets) + [int(extent + (extent & 1))]
+    assert tfl.RaggedPlan(big, offs, "complex64", "forward", "off").info()["single_launch"] == 0
