@@ -11,9 +11,9 @@ const KernelEntry* entries_f32_alt_cr(int* count) {
       make_entry<Cfg<float, 256, 16, 16, KIND_ROW>>(), make_entry<Cfg<float, 256, 16, 4, KIND_ROW>>(),
       // fewer columns / rows per block for the 512..2048 passes of larger N
       // (two or more blocks per SM instead of one)
-      make_entry<Cfg<float, 512, 16, 8, KIND_COL>>(),  make_entry<Cfg<float, 512, 16, 4, KIND_COL>>(),
+      make_entry<Cfg<float, 512, 16, 16, KIND_COL>>(), make_entry<Cfg<float, 512, 16, 4, KIND_COL>>(),
       make_entry<Cfg<float, 1024, 16, 4, KIND_COL>>(), make_entry<Cfg<float, 1024, 16, 2, KIND_COL>>(),
-      make_entry<Cfg<float, 2048, 16, 2, KIND_COL>>(), make_entry<Cfg<float, 512, 16, 8, KIND_ROW>>(),
+      make_entry<Cfg<float, 2048, 16, 2, KIND_COL>>(), make_entry<Cfg<float, 512, 16, 16, KIND_ROW>>(),
       make_entry<Cfg<float, 512, 16, 4, KIND_ROW>>(),  make_entry<Cfg<float, 1024, 16, 4, KIND_ROW>>(),
       make_entry<Cfg<float, 1024, 16, 2, KIND_ROW>>(), make_entry<Cfg<float, 2048, 16, 2, KIND_ROW>>(),
       // first pass of 8192 = 64 x 128 (ragged plans run by one launch)

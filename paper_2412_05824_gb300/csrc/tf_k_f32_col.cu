@@ -4,7 +4,7 @@ namespace tf {
 const KernelEntry* entries_f32_col(int* count) {
   static const KernelEntry t[] = {
       make_entry<Cfg<float, 128, 16, 16, KIND_COL>>(),  make_entry<Cfg<float, 256, 16, 8, KIND_COL>>(),
-      make_entry<Cfg<float, 512, 16, 16, KIND_COL>>(),  make_entry<Cfg<float, 1024, 16, 8, KIND_COL>>(),
+      make_entry<Cfg<float, 512, 16, 8, KIND_COL>>() ,  make_entry<Cfg<float, 1024, 16, 8, KIND_COL>>(),
       make_entry<Cfg<float, 2048, 16, 4, KIND_COL>>(),  make_entry<Cfg<float, 4096, 16, 2, KIND_COL>>(),
   };
   *count = sizeof(t) / sizeof(t[0]);

@@ -130,9 +130,10 @@ bool rg_setup(turbofft_plan* p) {
       r->ca_phase.push_back(phase);
       r->ca_units.push_back(units);
       smem = std::max(smem, (size_t)(r->ftm ? std::max(ci[c].smem_ft, ci[c].smem_fix) : ci[c].smem_plain));
-      // items of about 256 KB of input, whole checksum groups of T units
+      // items of about 512 KB of input (each item restarts the block's
+      // copy pipeline), whole checksum groups of T units
       const long long ubytes = (long long)ci[c].s * ci[c].ns * 8;
-      long long per = std::max<long long>(1, (256 << 10) / ubytes);
+      long long per = std::max<long long>(1, (512 << 10) / ubytes);
       per = (per + m->T - 1) / m->T * m->T;
       for (long long u = 0; u < units; u += per)
         pieces[phase].push_back({ca, u, std::min(units, u + per), ubytes * (std::min(units, u + per) - u)});
