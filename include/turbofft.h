@@ -75,7 +75,11 @@ typedef enum {
 typedef enum {
   TURBOFFT_FT_OFF = 0,            /* plain FFT, no checksums */
   TURBOFFT_FT_DETECT = 1,         /* checksums fused; detect and locate, report only */
-  TURBOFFT_FT_CORRECT = 2,        /* detect, locate and correct in place (Sec. 4.1.2) */
+  TURBOFFT_FT_CORRECT = 2,        /* detect, locate and correct in place (Sec. 4.1.2); F64
+                                     two-pass plans check and correct whole transforms
+                                     (one checksum pair per transform over both passes,
+                                     a failing transform recomputed); others check each
+                                     pass's sub-transforms in groups */
   TURBOFFT_FT_CORRECT_REGISTERS = 3, /* CORRECT, with the right-side sums accumulated in
                                         registers during the transform (the thread-level
                                         accumulation of Sec. 4.3) instead of formed from the

@@ -36,7 +36,7 @@ bool use_entry(turbofft_plan* p, int pi, const KernelEntry* ke) {
     return false;
   }
   p->pass[pi].ke = ke;
-  p->pass[pi].grid = occupancy_blocks(ke, ft_variant(p->ft_mode)) * g_num_sms;
+  p->pass[pi].grid = occupancy_blocks(ke, plan_variant(p)) * g_num_sms;
   return true;
 }
 
@@ -79,7 +79,7 @@ void autotune(turbofft_plan* p, const void* in, void* out, void* scratch) {
     const PassPlan& pp = p->pass[pi];
     std::vector<const KernelEntry*> cands = reg.find_all(dt, pp.kind, pp.ns);
     if (cands.size() < 2) continue;
-    const TuneKey key(dt, pi, p->n, p->batch, ft_variant(p->ft_mode), p->d_tab ? 1 : 0);
+    const TuneKey key(dt, pi, p->n, p->batch, plan_variant(p), p->d_tab ? 1 : 0);
     {
       std::lock_guard<std::mutex> lock(g_tune_mu);
       auto it = g_tune_cache.find(key);
@@ -92,7 +92,7 @@ void autotune(turbofft_plan* p, const void* in, void* out, void* scratch) {
     const KernelEntry* best = nullptr;
     float best_ms = 0.f;
     for (const KernelEntry* ke : cands) {
-      if (!ke->main[ft_variant(p->ft_mode)]) continue;  // no kernel of this checksum variant
+      if (!ke->main[plan_variant(p)]) continue;  // no kernel of this checksum variant
       if (!use_entry(p, pi, ke)) continue;
       bool ok = queue_plan(p, in, out, scratch, s, none) == TURBOFFT_SUCCESS;  // warm-up
       float ms_min = 0.f;

@@ -42,7 +42,7 @@ void add_report(const turbofft_plan* m, const std::vector<int64_t>* ids, turboff
     }
     if (rc.signal >= 0 && r->first_transform < 0) {
       // cluster plans record the transform itself
-      int64_t tr = m->cl ? rc.signal : rc.signal / signals_per_transform(m, rc.pass_id);
+      int64_t tr = (m->cl || m->tchk) ? rc.signal : rc.signal / signals_per_transform(m, rc.pass_id);
       tr += rc.transform_base;
       r->first_transform = (ids && tr >= 0 && tr < (int64_t)ids->size()) ? (*ids)[tr] : tr;
     }
@@ -235,9 +235,12 @@ turbofft_status create_plan(int64_t n, int64_t batch, turbofft_dtype dtype, int 
     }
     p->cl_grid = ncl * ce->cluster;
   }
+  // float64 two-pass plans with checksums check whole transforms
+  p->tchk = dt == 1 && p->num_passes == 2 && !p->cl && !t_ragged_member &&
+            (ft_mode == TURBOFFT_FT_DETECT || ft_mode == TURBOFFT_FT_CORRECT);
   for (int pi = 0; pi < p->num_passes && !p->cl; ++pi) {
     PassPlan& pp = p->pass[pi];
-    pp.ke = reg.find_variant(dt, pp.kind, pp.ns, ft_variant(ft_mode));
+    pp.ke = reg.find_variant(dt, pp.kind, pp.ns, plan_variant(p));
     if (!pp.ke) {
       turbofft_destroy(p);
       return TURBOFFT_UNSUPPORTED;
@@ -247,7 +250,7 @@ turbofft_status create_plan(int64_t n, int64_t batch, turbofft_dtype dtype, int 
       turbofft_destroy(p);
       return TURBOFFT_CUDA_ERROR;
     }
-    const int occ = occupancy_blocks(pp.ke, ft_variant(ft_mode));
+    const int occ = occupancy_blocks(pp.ke, plan_variant(p));
     pp.grid = occ * g_num_sms;
     pp.tau_coef = kGamma[dt] * kUnitRoundoff[dt] * sqrt((double)ilog2_exact(pp.ns));
     if (ft_mode == TURBOFFT_FT_CORRECT_THREAD) pp.tau_coef *= kThreadLevelGammaFactor;
@@ -271,9 +274,14 @@ turbofft_status create_plan(int64_t n, int64_t batch, turbofft_dtype dtype, int 
       ok = (dt == 0)   ? (upload<float>(p, lo_dst, lo) && upload<float>(p, hi_dst, hi))
            : (dt == 2) ? (upload_pairs(p, lo_dst, lo) && upload_pairs(p, hi_dst, hi))
                        : (upload<double>(p, lo_dst, lo) && upload<double>(p, hi_dst, hi));
-      if (ok && dt == 1 && !p->cl) ok = col_tables(p, p->pass[pi], ft_mode != TURBOFFT_FT_OFF);
+      if (ok && dt == 1 && !p->cl) ok = col_tables(p, p->pass[pi], ft_mode != TURBOFFT_FT_OFF && !p->tchk);
     }
     p->scratch_bytes = p->cl ? 0 : (size_t)(batch * n) * elem_bytes(dtype);
+    if (ok && p->tchk) {
+      void* acc = nullptr;
+      ok = tc_tables(p) && dev_alloc(p, &acc, (size_t)batch * 6 * sizeof(double));
+      p->d_tacc = static_cast<double*>(acc);
+    }
     if (!ok) {
       turbofft_destroy(p);
       return TURBOFFT_ALLOC_FAILED;

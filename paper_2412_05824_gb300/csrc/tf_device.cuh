@@ -455,6 +455,10 @@ struct Geo {
   // k' of row b goes to k1 + outer * k' of transform t (0 or 1: no mapping)
   int outer;
   long long n_outer;
+  // float64 column passes: 1 = units walk the transforms fastest (shared
+  // column tables), 0 = the columns of one transform first (transform-level
+  // checksums accumulate per transform)
+  int col_tfast;
 };
 
 __device__ __forceinline__ long long tr_base(const long long* tab, long long b, long long n) {
@@ -478,7 +482,7 @@ template <class K> __device__ __forceinline__ long long row_unit_first(const Geo
 // float32 column passes (no such tables) walk the columns of a transform.
 template <class K>
 __device__ __forceinline__ void col_unit(const Geo& g, long long unit, long long& b, int& c0) {
-  if constexpr (std::is_same<typename K::real, double>::value) {
+  if (std::is_same<typename K::real, double>::value && g.col_tfast) {
     const long long cb = unit / g.batch;
     b = unit - cb * g.batch;
     c0 = (int)cb * K::S;
@@ -603,6 +607,13 @@ template <typename R> struct PassArgs {
   int pass_id;
   long long transform_base;  // first transform of this launch in the caller's batch
   FtState* fts;
+  // transform-level checksums (float64 two-pass plans): per transform
+  // [v.x re, v.x im, e.y re, e.y im, energy, -], and the N-point weights in
+  // the passes' access orders: vcol[n2 * N1 + p] = v[p * N2 + n2],
+  // erow[k1 * N2 + k2] = e[k1 + N1 * k2]
+  double* tacc;
+  const c* vcol;
+  const c* erow;
   void* rec_sums; // MAX_RECORDS x 2 x NS_MAX complex (x_bar, y_bar)
   int rec_stride; // complex elements per record half (NS_MAX)
   InjectSite inj;
@@ -857,12 +868,23 @@ __device__ __forceinline__ void atomic_max_nonneg(float* addr, float v) {
 // ---------------------------------------------------------------------------
 // the transform kernel (one pass)
 // ---------------------------------------------------------------------------
+template <class K> __device__ __forceinline__ void block_sum3(double* red, double& a, double& b, double& c3);
+
+// transform of work unit `unit` of a column / row pass
+template <class K> __device__ __forceinline__ long long unit_transform(const Geo& g, long long unit) {
+  const long long sig = signal_of<K>(g, unit, 0);
+  return K::KIND == KIND_COL ? sig / g.n2 : sig / g.n1;
+}
+
 // FTM: 0 = no checksums; 1 = checksums, right-side sums formed on the rare
 // path from HBM; 2 = checksums, right-side sums kept in registers during the
 // pass (the thread-level accumulation of Sec. 4.3); 3 = thread-level ABFT
 // (Sec. 4.2.1): every thread checks its own whole transform against a
 // per-transform threshold, with no block reduction; a failing transform is
-// recorded for the correction kernel, which recomputes it
+// recorded for the correction kernel, which recomputes it; 4 = transform-level
+// checksums of a float64 two-pass plan: the column pass accumulates v.x and
+// the input energy of every transform, the row pass e.y, each over whole
+// transforms (N-point weights), and a check kernel compares them afterwards
 //
 // pass_body: the block's share of a pass, the work units first, first +
 // stride, ... below end (the pass kernel: blockIdx.x, gridDim.x, all units;
@@ -878,7 +900,12 @@ __device__ __forceinline__ void pass_body(const PassArgs<typename K::real>& A, c
   constexpr bool FT = FTM != 0;
   constexpr bool EAGER = FTM == 2;
   constexpr bool TL = FTM == 3;
+  constexpr bool TC = FTM == 4;
   static_assert(!TL || thread_level_ok<K>(), "thread-level checksums need one thread per transform");
+  static_assert(!TC || (std::is_same<R, double>::value && K::KIND != KIND_SP && !paired_ft<K>()),
+                "transform-level checksums: float64 column and row passes");
+  __shared__ double tc_red[TC ? 3 * 32 : 1];
+  double tc0 = 0, tc1 = 0, tc2 = 0;  // this block's sums for the current transform
 
   const int tid = threadIdx.x;
   const int slot = K::SLOT_FAST ? (tid % S) : (tid / P);
@@ -893,7 +920,7 @@ __device__ __forceinline__ void pass_body(const PassArgs<typename K::real>& A, c
   const c* __restrict__ vvp = A.vv;
   const float4* __restrict__ ev4p = A.ev4;
   const float4* __restrict__ vv4p = A.vv4;
-  if constexpr (FT && ev_in_smem<K>()) {
+  if constexpr (FT && !TC && ev_in_smem<K>()) {
     if constexpr (paired_ft<K>()) {
       float4* evs = reinterpret_cast<float4*>(smem_raw + NSTAGE * stage_bytes<K>());
       float4* vvs = evs + K::NS;
@@ -976,7 +1003,28 @@ __device__ __forceinline__ void pass_body(const PassArgs<typename K::real>& A, c
     // ---- input side of the checksums
     if constexpr (TL) en = 0;  // per-transform threshold
     c pin = mk<c>(0, 0);
-    if constexpr (FT) {
+    if constexpr (TC && K::KIND == KIND_COL) {
+      // v.x with the N-point weights in access order, and the energy (in
+      // float32 from integer-extracted bits, as below)
+      const long long vb = col_of<K>(g, valid ? sig : 0) * K::NS;
+      float enf = 0.f;
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        cmac(pin, ldg(A.vcol + vb + t + i * P), a[i]);
+        const float fx = abs_as_float(a[i].x), fy = abs_as_float(a[i].y);
+        enf = fmaf(fx, fx, enf);
+        enf = fmaf(fy, fy, enf);
+      }
+      double et = enf;
+      if (!isfinite(enf)) {
+        et = 0;
+#pragma unroll
+        for (int i = 0; i < E; ++i) et = fma(a[i].x, a[i].x, fma(a[i].y, a[i].y, et));
+      }
+      tc0 += pin.x;
+      tc1 += pin.y;
+      tc2 += et;
+    } else if constexpr (FT && !TC) {
       if constexpr (paired_ft<K>()) {
         // (sum v.re x, sum v.im x) with x = (re, im): two FFMA2 per element
         float2 q1 = make_float2(0.f, 0.f), q2 = make_float2(0.f, 0.f), e2 = make_float2(0.f, 0.f);
@@ -1060,7 +1108,7 @@ __device__ __forceinline__ void pass_body(const PassArgs<typename K::real>& A, c
             // loads) instead of two complex products per value
             const long long cw = col_of<K>(g, valid ? sig : 0) * K::NS + pos;
             a[i] = cmul(a[i], ldg(A.colw + cw));
-            if constexpr (FT) cmac(pout, ldg(A.colwe + cw), a[i]);
+            if constexpr (FT && !TC) cmac(pout, ldg(A.colwe + cw), a[i]);
           } else {
             const c w = colTwiddle<K>(g, A.tlo, A.thi, valid ? sig : 0, pos);
             a[i] = cmul(a[i], w);
@@ -1068,7 +1116,13 @@ __device__ __forceinline__ void pass_body(const PassArgs<typename K::real>& A, c
           }
         } else {
           if constexpr (EAGER) ys[i] = cadd(ys[i], a[i]);
-          if constexpr (FT) cmac(pout, weight<K>(evp, pos), a[i]);
+          if constexpr (TC) {
+            // e.y with the N-point weights of row k1 (contiguous)
+            const long long k1 = valid ? sig - (sig / g.n1) * g.n1 : 0;
+            cmac(pout, ldg(A.erow + k1 * K::NS + pos), a[i]);
+          } else if constexpr (FT) {
+            cmac(pout, weight<K>(evp, pos), a[i]);
+          }
         }
       }
     } else if constexpr (FT) {
@@ -1186,8 +1240,28 @@ __device__ __forceinline__ void pass_body(const PassArgs<typename K::real>& A, c
         }
       }
     }
+    // ---- transform-level sums: flushed when the next unit belongs to
+    // another transform (a uniform decision: a unit is one transform's)
+    if constexpr (TC) {
+      if constexpr (K::KIND == KIND_ROW) {
+        tc0 += pout.x;
+        tc1 += pout.y;
+      }
+      const long long tb = unit_transform<K>(g, unit);
+      const long long nx = unit + stride;
+      if (nx >= end || unit_transform<K>(g, nx) != tb) {
+        block_sum3<K>(tc_red, tc0, tc1, tc2);
+        if (tid == 0) {
+          double* acc = A.tacc + tb * 6 + (K::KIND == KIND_COL ? 0 : 2);
+          atomicAdd(acc, tc0);
+          atomicAdd(acc + 1, tc1);
+          if constexpr (K::KIND == KIND_COL) atomicAdd(A.tacc + tb * 6 + 4, tc2);
+        }
+        tc0 = tc1 = tc2 = 0;
+      }
+    }
     // ---- per-transaction checksum residual, location encoding
-    if constexpr (FT && !TL) {
+    if constexpr (FT && !TL && !TC) {
       const R rr = pout.x - pin.x, ri = pout.y - pin.y;
       if (!(isfinite(rr) && isfinite(ri))) {
         bad_lo = min(bad_lo, gi);
@@ -1200,7 +1274,7 @@ __device__ __forceinline__ void pass_body(const PassArgs<typename K::real>& A, c
     }
     ++gi;
     const bool group_end = (gi == A.T) || (unit + stride >= end);
-    if constexpr (FT && !TL) {
+    if constexpr (FT && !TL && !TC) {
       if (group_end) {
         // ---- reduce the group over the threads of each slot.  Phase 1
         // reduces S1 and the energy in the working precision and clears
@@ -1344,7 +1418,7 @@ __device__ __forceinline__ void pass_body(const PassArgs<typename K::real>& A, c
       if (total) atomicAdd(&A.fts->groups, (unsigned long long)total);
       if (mr) atomic_max_nonneg(&A.fts->max_clean_ratio, __uint_as_float(mr));
     }
-  } else if constexpr (FT) {
+  } else if constexpr (FT && !TC) {
     if (tid == 0 && groups > 0) atomicAdd(&A.fts->groups, (unsigned long long)(groups * S));
     if (tid < S && max_ratio2 > 0.f) atomic_max_nonneg(&A.fts->max_clean_ratio, sqrtf(max_ratio2));
   }
@@ -1354,7 +1428,48 @@ template <class K, int FTM>
 __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_FT : TwMode<K>::MINB)
     tf_pass_kernel(const PassArgs<typename K::real> A) {
   extern __shared__ __align__(128) unsigned char smem_raw_[];
-  pass_body<K, FTM>(A, reinterpret_cast<char*>(smem_raw_), blockIdx.x, gridDim.x, A.num_units);
+  if constexpr (FTM == 4) {
+    // transform-level checksums: each block takes one contiguous range of
+    // units, so its sums change transform only at range boundaries
+    const long long per = (A.num_units + gridDim.x - 1) / gridDim.x;
+    const long long first = (long long)blockIdx.x * per;
+    pass_body<K, FTM>(A, reinterpret_cast<char*>(smem_raw_), first, 1,
+                      first + per < A.num_units ? first + per : A.num_units);
+  } else {
+    pass_body<K, FTM>(A, reinterpret_cast<char*>(smem_raw_), blockIdx.x, gridDim.x, A.num_units);
+  }
+}
+
+// Transform-level correction (float64 two-pass plans): the transforms the
+// check kernel recorded are recomputed from their untouched input, this
+// pass's units of each shared by all blocks of the grid (the column pass in
+// one launch, the row pass in the next).  The recompute runs without the
+// armed fault site.  The row launch (block 0) counts each recorded
+// transform as corrected.  Transform-level records are those with
+// unit_stride 0 (block-level records hold the stride of their units).
+template <class K>
+__global__ void __launch_bounds__(K::NT) tf_tc_fix_kernel(const PassArgs<typename K::real> A) {
+  extern __shared__ __align__(128) unsigned char smem_raw_[];
+  if (A.ft != FT_CORRECT) return;
+  const unsigned long long n = *reinterpret_cast<volatile unsigned long long*>(&A.fts->num_records);
+  const unsigned long long nrec = n < (unsigned long long)MAX_RECORDS ? n : (unsigned long long)MAX_RECORDS;
+  if (nrec == 0) return;
+  PassArgs<typename K::real> B = A;
+  B.inj.active = 0;
+  const long long ub = (K::KIND == KIND_COL ? A.geo.n2 : A.geo.n1) / K::S;  // units per transform
+  for (unsigned long long r = 0; r < nrec; ++r) {
+    volatile FtRecord& rec = A.fts->rec[r];
+    if (rec.unit_stride != 0) continue;  // not a transform-level record
+    const long long b = rec.signal;
+    __syncthreads();
+    pass_body<K, 0>(B, reinterpret_cast<char*>(smem_raw_), b * ub + blockIdx.x, gridDim.x, (b + 1) * ub);
+    if (K::KIND == KIND_ROW && blockIdx.x == 0 && threadIdx.x == 0) {
+      rec.result = FT_RES_RECOMPUTE;
+      atomicAdd(&A.fts->located, 1ull);
+      atomicAdd(&A.fts->corrected, 1ull);
+      atomicAdd(&A.fts->recomputed, 1ull);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------

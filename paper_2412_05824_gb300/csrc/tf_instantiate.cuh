@@ -13,6 +13,12 @@ template <class K, int FTM> void launch_main(const void* a, int grid, cudaStream
 template <class K> void launch_fix(const void* a, int grid, cudaStream_t s) {
   tf_fix_kernel<K><<<grid, K::NT, K::SMEM_BYTES, s>>>(*static_cast<const PassArgs<typename K::real>*>(a));
 }
+template <class K> void launch_tcfix(const void* a, int grid, cudaStream_t s) {
+  tf_tc_fix_kernel<K><<<grid, K::NT, pass_smem_bytes<K, 0>(), s>>>(*static_cast<const PassArgs<typename K::real>*>(a));
+}
+template <class K> constexpr bool transform_level_ok() {
+  return std::is_same<typename K::real, double>::value && K::KIND != KIND_SP;
+}
 
 template <class K> KernelEntry make_entry() {
   KernelEntry e;
@@ -45,6 +51,20 @@ template <class K> KernelEntry make_entry() {
     e.main[3] = nullptr;
     e.fn_main[3] = nullptr;
   }
+  // transform-level checksums of float64 two-pass plans
+  if constexpr (transform_level_ok<K>()) {
+    e.smem_main[4] = pass_smem_bytes<K, 4>();
+    e.main[4] = &launch_main<K, 4>;
+    e.fn_main[4] = reinterpret_cast<const void*>(&tf_pass_kernel<K, 4>);
+    e.tcfix = &launch_tcfix<K>;
+    e.fn_tcfix = reinterpret_cast<const void*>(&tf_tc_fix_kernel<K>);
+  } else {
+    e.smem_main[4] = 0;
+    e.main[4] = nullptr;
+    e.fn_main[4] = nullptr;
+    e.tcfix = nullptr;
+    e.fn_tcfix = nullptr;
+  }
   return e;
 }
 
@@ -61,7 +81,9 @@ template <class K> KernelEntry make_entry_plain() {
   e.smem_main[0] = pass_smem_bytes<K, 0>();
   e.main[0] = &launch_main<K, 0>;
   e.fn_main[0] = reinterpret_cast<const void*>(&tf_pass_kernel<K, 0>);
-  for (int v = 1; v < 4; ++v) {
+  e.tcfix = nullptr;
+  e.fn_tcfix = nullptr;
+  for (int v = 1; v < 5; ++v) {
     e.smem_main[v] = 0;
     e.main[v] = nullptr;
     e.fn_main[v] = nullptr;

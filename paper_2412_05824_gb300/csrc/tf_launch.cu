@@ -33,6 +33,7 @@ int ft_variant(int ft_mode) {
 }
 
 int kernel_dtype(const turbofft_plan* p) { return p->dtype == TURBOFFT_C2C_F32 ? 0 : (p->pairs ? 2 : 1); }
+int plan_variant(const turbofft_plan* p) { return p->tchk ? 4 : ft_variant(p->ft_mode); }
 
 // cluster kernels have no register-sums variant: that mode runs as CORRECT
 int cl_variant(int ft_mode) { return ft_mode == TURBOFFT_FT_OFF ? 0 : 1; }
@@ -49,12 +50,15 @@ int occupancy_blocks(const KernelEntry* ke, int variant) {
 
 bool set_smem_attrs(const KernelEntry* ke) {
   // the attribute is per function; setting it again is harmless
-  for (int v = 0; v < 4; ++v)
+  for (int v = 0; v < 5; ++v)
     if (ke->fn_main[v] && cudaFuncSetAttribute(ke->fn_main[v], cudaFuncAttributeMaxDynamicSharedMemorySize, ke->smem_main[v]) !=
         cudaSuccess)
       return false;
   if (ke->fn_fix &&
       cudaFuncSetAttribute(ke->fn_fix, cudaFuncAttributeMaxDynamicSharedMemorySize, ke->smem_fix) != cudaSuccess)
+    return false;
+  if (ke->fn_tcfix && cudaFuncSetAttribute(ke->fn_tcfix, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           ke->smem_main[0]) != cudaSuccess)
     return false;
   return true;
 }
@@ -74,6 +78,50 @@ int64_t signals_per_transform(const turbofft_plan* p, int pi) {
 }
 
 namespace {
+
+// Transform-level check of float64 two-pass plans: one thread per transform
+// compares e.y (row pass) with v.x (column pass) against
+// tau = gamma u sqrt(log2 N) sqrt(N energy); a mismatch appends a record
+// (unit_stride 0, signal = the transform) for the recompute kernels.
+__global__ void tc_check_kernel(const double* tacc, long long batch, double tau_coef, double n, tf::FtState* fts,
+                                int correct, long long tbase) {
+  float mr = 0.f;
+  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < batch;
+       b += (long long)gridDim.x * blockDim.x) {
+    const double* a = tacc + b * 6;
+    const double rr = a[2] - a[0], ri = a[3] - a[1];
+    const double tau = tau_coef * sqrt(n * a[4]);
+    const double mag = sqrt(rr * rr + ri * ri);
+    if (isfinite(mag) && isfinite(tau) && mag <= tau) {
+      if (tau > 0) mr = fmaxf(mr, (float)(mag / tau));
+      continue;
+    }
+    atomicAdd(&fts->detected, 1ull);
+    if (!correct) atomicAdd(&fts->located, 1ull);
+    const unsigned long long r = atomicAdd(&fts->num_records, 1ull);
+    if (r < (unsigned long long)tf::MAX_RECORDS) {
+      tf::FtRecord& R0 = fts->rec[r];
+      R0.pass_id = 1;
+      R0.slot = 0;
+      R0.count = 1;
+      R0.located = 0;
+      R0.unit0 = b;
+      R0.unit_stride = 0;
+      R0.transform_base = tbase;
+      R0.s1r = rr; R0.s1i = ri; R0.s2r = rr; R0.s2i = ri;
+      R0.tau = tau;
+      R0.energy = a[4];
+      R0.result = correct ? tf::FT_RES_PENDING : tf::FT_RES_LOCATED;
+      R0.has_sums = 0;
+      R0.signal = b;
+    } else {
+      atomicAdd(&fts->dropped, 1ull);
+    }
+  }
+  const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(mr));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(reinterpret_cast<int*>(&fts->max_clean_ratio), (int)m);
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&fts->groups, (unsigned long long)batch);
+}
 
 template <typename R>
 void fill_args(const turbofft_plan* p, int pi, const void* in, void* out, int64_t batch, int64_t tbase,
@@ -115,6 +163,10 @@ void fill_args(const turbofft_plan* p, int pi, const void* in, void* out, int64_
   A.pass_id = pi;
   A.transform_base = tbase;
   A.fts = p->d_fts;
+  A.tacc = p->d_tacc;
+  A.vcol = static_cast<const c*>(p->d_vcol);
+  A.erow = static_cast<const c*>(p->d_erow);
+  A.geo.col_tfast = p->tchk ? 0 : 1;
   A.rec_sums = p->d_rec_sums;
   A.rec_stride = p->rec_stride;
   A.inj = inj;
@@ -238,8 +290,22 @@ turbofft_status run(turbofft_plan* p, const void* in, void* out, void* scratch, 
     } else {
       tf::PassArgs<double> A;
       fill_args<double>(p, pi, pin, pout, batch, tbase, inj, A);
-      timed(2 * pi, [&] { pp.ke->main[ft_variant(p->ft_mode)](&A, grid, stream); });
-      if (ft) timed(2 * pi + 1, [&] { pp.ke->fix(&A, 8, stream); });
+      timed(2 * pi, [&] { pp.ke->main[plan_variant(p)](&A, grid, stream); });
+      if (ft && !p->tchk) timed(2 * pi + 1, [&] { pp.ke->fix(&A, 8, stream); });
+      if (p->tchk && pi == p->num_passes - 1) {
+        // compare the whole transforms' sums, then recompute the recorded
+        // transforms: column pass, then row pass
+        const double tau = kGamma[1] * kUnitRoundoff[1] * sqrt((double)ilog2_exact(p->n)) * p->threshold_scale;
+        const int cgrid = (int)std::min<long long>((batch + 255) / 256, 1024);
+        timed(2 * pi + 1, [&] {
+          tc_check_kernel<<<cgrid, 256, 0, stream>>>(p->d_tacc, batch, tau, (double)p->n, p->d_fts,
+                                                      p->ft_mode == TURBOFFT_FT_DETECT ? 0 : 1, tbase);
+          tf::PassArgs<double> A0;
+          fill_args<double>(p, 0, in, scratch, batch, tbase, inj, A0);
+          p->pass[0].ke->tcfix(&A0, p->pass[0].grid, stream);
+          pp.ke->tcfix(&A, pp.grid, stream);
+        });
+      }
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(p, e, "kernel launch");
@@ -256,6 +322,7 @@ turbofft_status queue_plan(turbofft_plan* p, const void* in, void* out, void* sc
   const bool ft = p->ft_mode != TURBOFFT_FT_OFF;
   if (ft) {
     cudaError_t e = cudaMemsetAsync(p->d_fts, 0, tf::FT_HEADER_BYTES, s);
+    if (e == cudaSuccess && p->tchk) e = cudaMemsetAsync(p->d_tacc, 0, (size_t)p->batch * 6 * sizeof(double), s);
     if (e != cudaSuccess) return cuda_fail(p, e, "report reset");
   }
   turbofft_status st = run(p, in, out, scratch, p->batch, 0, s, inj);

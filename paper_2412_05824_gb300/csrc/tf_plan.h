@@ -157,6 +157,12 @@ struct turbofft_plan {
   int64_t n = 0, batch = 0;
   int dtype = 0, direction = -1, ft_mode = 0;
   bool pairs = false;  // float64 data transformed in float-pair arithmetic
+  // float64 two-pass plan with checksums over whole transforms (column pass
+  // v.x, row pass e.y, check and recompute kernels after the row pass)
+  bool tchk = false;
+  void* d_vcol = nullptr;
+  void* d_erow = nullptr;
+  double* d_tacc = nullptr;
   int device = 0;
   int num_passes = 1;
   int n1 = 0, n2 = 1;
@@ -226,12 +232,14 @@ bool upload(turbofft_plan* p, void** dst, const std::vector<cld>& v) {
 bool upload_pairs(turbofft_plan* p, void** dst, const std::vector<cld>& v);
 bool upload_tables(turbofft_plan* p, PassPlan& pp);
 bool col_tables(turbofft_plan* p, PassPlan& pp, bool weights);  // float64 column-pass tables, host-built
+bool tc_tables(turbofft_plan* p);  // N-point weights of transform-level checksums, host-built
 
 // ---------------------------------------------------------------------------
 // launches (tf_launch.cu)
 // ---------------------------------------------------------------------------
 int ft_variant(int ft_mode);   // 0 none, 1 checksums, 2 checksums + register sums, 3 thread-level
 int kernel_dtype(const turbofft_plan* p);  // registry dtype: 0 float32, 1 float64, 2 float pairs
+int plan_variant(const turbofft_plan* p);  // kernel variant of the plan's passes (4: transform-level)
 int cl_variant(int ft_mode);   // cluster kernels: 0 none, 1 checksums
 int occupancy_blocks(const KernelEntry* ke, int variant);
 bool set_smem_attrs(const KernelEntry* ke);

@@ -15,14 +15,17 @@ struct KernelEntry {
   int s;            // sub-transforms per transaction
   int nt;           // threads per block
   int stages;       // radix passes
-  int smem_main[4]; // dynamic shared memory of the transform kernel per variant
+  int smem_main[5]; // dynamic shared memory of the transform kernel per variant
   int smem_fix;     // dynamic shared memory of the correction kernel
   // transform kernel: no checksums / checksums / checksums + register sums /
-  // thread-level checksums (one thread per transform only; null otherwise)
-  LaunchFn main[4];
+  // thread-level checksums (one thread per transform only; null otherwise) /
+  // transform-level checksums (float64 column and row passes; null otherwise)
+  LaunchFn main[5];
   LaunchFn fix;       // correction kernel
-  const void* fn_main[4];
+  LaunchFn tcfix;     // transform-level correction: recompute recorded transforms' pass
+  const void* fn_main[5];
   const void* fn_fix;
+  const void* fn_tcfix;
 };
 
 // all entries of one translation unit

@@ -222,4 +222,88 @@ bool col_tables(turbofft_plan* p, PassPlan& pp, bool weights) {
   return true;
 }
 
+// N-point weights of transform-level checksums (float64 two-pass plans).
+// e: N unit-modulus phases (SplitMix64 from the seed of the block-level
+// vectors, in float64); v = W e by a float64 radix-2 FFT on the host whose
+// twiddles w_N^j are double-double products of two long-double tables
+// rounded once (v is only needed consistent with e to the float64
+// transform's own rounding level).  Stored in the passes' access orders:
+// vcol[n2 * N1 + p] = v[p * N2 + n2] (column pass), erow[k1 * N2 + k2] =
+// e[k1 + N1 * k2] (row pass).
+bool tc_tables(turbofft_plan* p) {
+  const int64_t N = p->n;
+  const int n1 = p->n1, n2 = p->n2;
+  std::vector<double> er((size_t)N), ei((size_t)N), vr, vi;
+  const uint64_t seed = 0x5EEDull;
+  for (int64_t j = 0; j < N; ++j) {
+    const uint64_t w = splitmix_mix(seed + (uint64_t)(j + 1) * 0x9E3779B97F4A7C15ull);
+    const double theta = (double)(w >> 11) * 0x1p-53;
+    er[(size_t)j] = std::cos(6.283185307179586476925 * theta);
+    ei[(size_t)j] = std::sin(6.283185307179586476925 * theta);
+  }
+  // twiddles w_N^j, j < N/2
+  const size_t half = (size_t)(N / 2);
+  std::vector<double> twr(half), twi(half);
+  {
+    const size_t nhi = std::max<size_t>(1, half / 4096 + 1);
+    std::vector<D2> lr(4096), li(4096), hr(nhi), hi(nhi);
+    for (int j = 0; j < 4096; ++j) {
+      const cld w = root(N, j);
+      lr[j] = d2_of(w.real());
+      li[j] = d2_of(w.imag());
+    }
+    for (size_t j = 0; j < nhi; ++j) {
+      const cld w = root(N, (int64_t)j * 4096);
+      hr[j] = d2_of(w.real());
+      hi[j] = d2_of(w.imag());
+    }
+    for (size_t j = 0; j < half; ++j) {
+      const size_t a = j >> 12, b = j & 4095u;
+      twr[j] = d2_round(d2_add(d2_mul(hr[a], lr[b]), d2_neg(d2_mul(hi[a], li[b]))));
+      twi[j] = d2_round(d2_add(d2_mul(hr[a], li[b]), d2_mul(hi[a], lr[b])));
+    }
+  }
+  // v = W e: bit-reversed order, then radix-2 butterflies
+  vr = er;
+  vi = ei;
+  for (size_t i = 1, j = 0; i < (size_t)N; ++i) {
+    size_t bit = (size_t)N >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) {
+      std::swap(vr[i], vr[j]);
+      std::swap(vi[i], vi[j]);
+    }
+  }
+  for (size_t len = 2; len <= (size_t)N; len <<= 1) {
+    const size_t h = len / 2, step = (size_t)N / len;
+    for (size_t i = 0; i < (size_t)N; i += len)
+      for (size_t k = 0; k < h; ++k) {
+        const double wr = twr[k * step], wi = twi[k * step];
+        const size_t q = i + k + h;
+        const double tr = vr[q] * wr - vi[q] * wi, ti = vr[q] * wi + vi[q] * wr;
+        vr[q] = vr[i + k] - tr;
+        vi[q] = vi[i + k] - ti;
+        vr[i + k] += tr;
+        vi[i + k] += ti;
+      }
+  }
+  std::vector<double2> vcol((size_t)N), erow((size_t)N);
+  for (int c = 0; c < n2; ++c)
+    for (int q = 0; q < n1; ++q) {
+      const size_t src = (size_t)q * n2 + c;
+      vcol[(size_t)c * n1 + q] = make_double2(vr[src], vi[src]);
+    }
+  for (int k1 = 0; k1 < n1; ++k1)
+    for (int k2 = 0; k2 < n2; ++k2) {
+      const size_t src = (size_t)k1 + (size_t)n1 * k2;
+      erow[(size_t)k1 * n2 + k2] = make_double2(er[src], ei[src]);
+    }
+  const size_t bytes = (size_t)N * sizeof(double2);
+  return dev_alloc(p, &p->d_vcol, bytes) &&
+         cudaMemcpy(p->d_vcol, vcol.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
+         dev_alloc(p, &p->d_erow, bytes) &&
+         cudaMemcpy(p->d_erow, erow.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
 }  // namespace tfh

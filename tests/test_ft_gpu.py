@@ -221,3 +221,28 @@ def test_exec_host_reports_and_corrects():
     rep = plan.report()
     assert rep["corrected"] >= 1 and rep["first_transform"] == 50
     assert float(np.max(oracle.rel_l2(y.numpy(), oracle.fft(x)))) <= oracle.tolerance(np.float32, n)
+
+
+@pytest.mark.parametrize("n,batch", [(1 << 13, 37), (1 << 16, 9), (1 << 20, 3)])
+def test_float64_two_pass_checks_whole_transforms(n, batch):
+    """float64 two-pass plans check whole transforms: v.x in the column pass,
+    e.y in the row pass, compared after it (one check per transform); a
+    fault in either pass is found on its transform and recomputed."""
+    r = Runner(n, batch, "c128")
+    _, err, rep = r.run("correct")
+    assert rep["detected"] == 0 and rep["groups_checked"] == batch
+    assert 0 < rep["max_clean_ratio"] < 0.8
+    assert float(np.max(err)) <= r.tol
+    rng = np.random.default_rng(n + 5)
+    for k in range(6):
+        p = k % 2
+        st = int(rng.integers(0, r.stages(p) + 1))
+        tr, el, comp = int(rng.integers(0, batch)), int(rng.integers(0, n)), int(rng.integers(0, 2))
+        y, err, rep = r.run("correct", (tr, p, st, el, comp), 62)
+        assert rep["detected"] == 1 and rep["corrected"] == 1 and rep["recomputed"] == 1, (p, st, rep)
+        assert rep["first_transform"] == tr and rep["first_pass"] == 1 and rep["uncorrectable"] == 0
+        assert float(np.max(err)) <= r.tol
+        # detect mode: reported on the transform, not corrected
+        _, err_d, rep_d = r.run("detect", (tr, p, st, el, comp), 62)
+        assert rep_d["detected"] == 1 and rep_d["located"] == 1 and rep_d["first_transform"] == tr
+        assert not (float(np.max(err_d)) <= r.tol)
