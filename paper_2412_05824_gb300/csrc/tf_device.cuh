@@ -1429,12 +1429,32 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
     tf_pass_kernel(const PassArgs<typename K::real> A) {
   extern __shared__ __align__(128) unsigned char smem_raw_[];
   if constexpr (FTM == 4) {
-    // transform-level checksums: each block takes one contiguous range of
-    // units, so its sums change transform only at range boundaries
-    const long long per = (A.num_units + gridDim.x - 1) / gridDim.x;
-    const long long first = (long long)blockIdx.x * per;
-    pass_body<K, FTM>(A, reinterpret_cast<char*>(smem_raw_), first, 1,
-                      first + per < A.num_units ? first + per : A.num_units);
+    // transform-level checksums: every block works on contiguous unit
+    // ranges of one transform at a time, so its sums change transform only
+    // at range boundaries
+    const long long ub = (K::KIND == KIND_COL ? A.geo.n2 : A.geo.n1) / K::S;  // units per transform
+    const long long batch = A.num_units / ub;
+    if (A.geo.n >= (1 << 20)) {
+      // large N: the N-point tables outgrow L2.  Items are a part of one
+      // transform, the transforms fastest, so the blocks running at once
+      // work on the same part (the same table entries) of different
+      // transforms; about 16 items per block keep the tail short.
+      long long parts = (16ll * gridDim.x + batch - 1) / batch;
+      if (parts > ub) parts = ub;
+      const long long items = batch * parts;
+      for (long long i = blockIdx.x; i < items; i += gridDim.x) {
+        const long long b = i % batch, part = i / batch;
+        __syncthreads();
+        pass_body<K, FTM>(A, reinterpret_cast<char*>(smem_raw_), b * ub + part * ub / parts, 1,
+                          b * ub + (part + 1) * ub / parts);
+      }
+    } else {
+      // one contiguous range of units per block (the tables fit in L2)
+      const long long per = (A.num_units + gridDim.x - 1) / gridDim.x;
+      const long long first = (long long)blockIdx.x * per;
+      pass_body<K, FTM>(A, reinterpret_cast<char*>(smem_raw_), first, 1,
+                        first + per < A.num_units ? first + per : A.num_units);
+    }
   } else {
     pass_body<K, FTM>(A, reinterpret_cast<char*>(smem_raw_), blockIdx.x, gridDim.x, A.num_units);
   }
