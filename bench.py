@@ -130,7 +130,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-KERNEL_HEADERS = ("tf_device.cuh", "tf_types.h", "tf_dft_constants.h", "tf_instantiate.cuh", "tf_registry.h")
+KERNEL_HEADERS = ("tf_device.cuh", "tf_dd.cuh", "tf_types.h", "tf_dft_constants.h", "tf_instantiate.cuh", "tf_registry.h")
 
 
 def src_hash(key=None):

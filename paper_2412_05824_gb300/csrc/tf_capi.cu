@@ -241,21 +241,6 @@ turbofft_status create_plan(int64_t n, int64_t batch, turbofft_dtype dtype, int 
   for (int pi = 0; pi < p->num_passes && !p->cl; ++pi) {
     PassPlan& pp = p->pass[pi];
     pp.ke = reg.find_variant(dt, pp.kind, pp.ns, plan_variant(p));
-    if (pp.ke && pp.kind == tf::KIND_SP && !t_ragged_member) {
-      // a small batch spreads over the SMs with fewer transforms per block:
-      // the same radix with the largest S that still gives 4 units per SM
-      // (or the smallest S there is)
-      const long long want = 4ll * g_num_sms;
-      if ((batch + pp.ke->s - 1) / pp.ke->s < want) {
-        const tf::KernelEntry* best = pp.ke;
-        for (const tf::KernelEntry* e : reg.find_all(dt, pp.kind, pp.ns)) {
-          if (!e->main[plan_variant(p)] || e->e != pp.ke->e || e->s >= pp.ke->s) continue;
-          const bool e_ok = (batch + e->s - 1) / e->s >= want, b_ok = (batch + best->s - 1) / best->s >= want;
-          if ((e_ok && (!b_ok || e->s > best->s)) || (!e_ok && !b_ok && e->s < best->s)) best = e;
-        }
-        pp.ke = best;
-      }
-    }
     if (!pp.ke) {
       turbofft_destroy(p);
       return TURBOFFT_UNSUPPORTED;
