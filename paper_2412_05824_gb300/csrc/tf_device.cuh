@@ -1466,7 +1466,8 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
 // one launch, the row pass in the next).  The recompute runs without the
 // armed fault site.  The row launch (block 0) counts each recorded
 // transform as corrected.  Transform-level records are those with
-// unit_stride 0 (block-level records hold the stride of their units).
+// unit_stride 0 (block-level records hold the stride of their units); a
+// record's transform_base tells the chunk of a chunked exec it belongs to.
 template <class K>
 __global__ void __launch_bounds__(K::NT) tf_tc_fix_kernel(const PassArgs<typename K::real> A) {
   extern __shared__ __align__(128) unsigned char smem_raw_[];
@@ -1479,7 +1480,9 @@ __global__ void __launch_bounds__(K::NT) tf_tc_fix_kernel(const PassArgs<typenam
   const long long ub = (K::KIND == KIND_COL ? A.geo.n2 : A.geo.n1) / K::S;  // units per transform
   for (unsigned long long r = 0; r < nrec; ++r) {
     volatile FtRecord& rec = A.fts->rec[r];
-    if (rec.unit_stride != 0) continue;  // not a transform-level record
+    // transform-level records of this launch's transforms only (a chunked
+    // exec appends the records of every chunk to one report)
+    if (rec.unit_stride != 0 || rec.transform_base != A.transform_base) continue;
     const long long b = rec.signal;
     __syncthreads();
     pass_body<K, 0>(B, reinterpret_cast<char*>(smem_raw_), b * ub + blockIdx.x, gridDim.x, (b + 1) * ub);

@@ -447,6 +447,10 @@ turbofft_status turbofft_exec_host(turbofft_plan* p, const void* host_in, void* 
       if (tr >= b0 && tr < b0 + nb) cinj.signal = inj.signal - b0 * per_tr;
       else cinj.active = 0;
     }
+    // whole-transform sums start at zero for every chunk (its transforms
+    // are indexed from 0)
+    if (p->tchk && (e = cudaMemsetAsync(p->d_tacc, 0, (size_t)nb * 6 * sizeof(double), sc)) != cudaSuccess)
+      return cuda_fail(p, e, "report reset");
     turbofft_status st = run(p, hs.in[sl], hs.out[sl], hs.scratch, nb, b0, sc, cinj);
     if (st != TURBOFFT_SUCCESS) return st;
     cudaEventRecord(ev[2 + sl], sc);

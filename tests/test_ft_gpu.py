@@ -246,3 +246,27 @@ def test_float64_two_pass_checks_whole_transforms(n, batch):
         _, err_d, rep_d = r.run("detect", (tr, p, st, el, comp), 62)
         assert rep_d["detected"] == 1 and rep_d["located"] == 1 and rep_d["first_transform"] == tr
         assert not (float(np.max(err_d)) <= r.tol)
+
+
+def test_float64_whole_transform_checks_through_host_chunks():
+    """Host-buffer exec of a float64 two-pass plan runs in chunks of about
+    64 MiB (here 4 transforms of 16 MiB): every chunk starts its whole-
+    transform sums from zero, and a fault in a later chunk is corrected once,
+    on its global transform index."""
+    n, batch = 1 << 20, 11
+    x = ss.uniform_complex(14, batch, n, np.float64)
+    ref = oracle.fft(x)
+    tol = oracle.tolerance(np.float64, n)
+    plan = tfl.Plan(n, batch, "complex128", "forward", "correct")
+    xh = torch.from_numpy(x).pin_memory()
+    for _ in range(2):
+        y = plan.exec_host(xh)
+        rep = plan.report()
+        assert rep["detected"] == 0 and rep["groups_checked"] == batch, rep
+        assert float(np.max(oracle.rel_l2(y.numpy(), ref))) <= tol
+    plan.inject(9, 1, 2, 12345, 0, 62)
+    y = plan.exec_host(xh)
+    rep = plan.report()
+    assert rep["detected"] == 1 and rep["corrected"] == 1 and rep["first_transform"] == 9, rep
+    assert float(np.max(oracle.rel_l2(y.numpy(), ref))) <= tol
+    plan.close()
