@@ -792,7 +792,9 @@ def run_ours(args):
     launches_per_step = 0
     for dt2, eb2, d2, n2 in cfgs:
         inf2 = plans_ft[(dt2, d2, n2)].info()
-        launches_per_step += 2 if inf2["cluster"] else inf2["num_passes"] * 2
+        # cluster: kernel + correction; whole-transform checks: two passes,
+        # check, two recompute kernels; else a kernel and a correction per pass
+        launches_per_step += 2 if inf2["cluster"] else (5 if inf2["transform_checks"] else inf2["num_passes"] * 2)
     sweep = []
     for i, (dt2, eb2, d2, n2) in enumerate(cfgs):
         b = 2.0 * ELEMENTS * eb2

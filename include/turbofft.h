@@ -169,6 +169,10 @@ typedef struct {
                                grid/block then describe that kernel */
   int32_t single_launch;    /* ragged plan: 1 if an exec is one launch of the persistent
                                ragged kernel, 0 if a graph of per-size kernels */
+  int32_t transform_checks; /* 1: checksums over whole transforms (F64 two-pass plans with
+                               DETECT / CORRECT): an exec launches the two passes, a check
+                               kernel and two recompute kernels */
+  int32_t reserved3;
 } turbofft_plan_info;
 
 /* Duration of one kernel of the last exec (turbofft_set_profiling). */

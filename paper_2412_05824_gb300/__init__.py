@@ -77,7 +77,8 @@ class PlanInfo(ctypes.Structure):
                 ("block", ctypes.c_int32 * 3), ("workspace_bytes", ctypes.c_int64),
                 ("scratch_bytes", ctypes.c_int64), ("per_block", ctypes.c_int32 * 3),
                 ("num_members", ctypes.c_int32), ("autotuned", ctypes.c_int32),
-                ("cluster", ctypes.c_int32), ("single_launch", ctypes.c_int32)]
+                ("cluster", ctypes.c_int32), ("single_launch", ctypes.c_int32),
+                ("transform_checks", ctypes.c_int32), ("reserved3", ctypes.c_int32)]
 
 
 class KernelTime(ctypes.Structure):

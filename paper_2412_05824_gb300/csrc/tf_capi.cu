@@ -68,6 +68,7 @@ void fill_info(const turbofft_plan* p, turbofft_plan_info* info) {
     return;
   }
   info->num_passes = p->num_passes;
+  info->transform_checks = p->tchk ? 1 : 0;
   if (p->cl) {
     const ClEntry* ce = p->cl;
     info->cluster = ce->cluster;

@@ -229,6 +229,8 @@ def test_float64_two_pass_checks_whole_transforms(n, batch):
     e.y in the row pass, compared after it (one check per transform); a
     fault in either pass is found on its transform and recomputed."""
     r = Runner(n, batch, "c128")
+    assert r.plans["correct"].info()["transform_checks"] == 1
+    assert r.plans["correct_registers"].info()["transform_checks"] == 0  # per-pass groups
     _, err, rep = r.run("correct")
     assert rep["detected"] == 0 and rep["groups_checked"] == batch
     assert 0 < rep["max_clean_ratio"] < 0.8
