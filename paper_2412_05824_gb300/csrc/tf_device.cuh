@@ -1435,18 +1435,21 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
     const long long ub = (K::KIND == KIND_COL ? A.geo.n2 : A.geo.n1) / K::S;  // units per transform
     const long long batch = A.num_units / ub;
     if (A.geo.n >= (1 << 20)) {
-      // large N: the N-point tables outgrow L2.  Items are a part of one
-      // transform, the transforms fastest, so the blocks running at once
-      // work on the same part (the same table entries) of different
-      // transforms; about 16 items per block keep the tail short.
+      // large N: the N-point tables outgrow L2, and the 16-byte columns /
+      // transposed rows of one-wide tiles share 32-byte sectors with their
+      // neighbours.  Item (b, p) is every parts-th unit of transform b from
+      // p on; the items run transforms fastest, so the blocks running at
+      // once hold adjacent units of every transform: neighbouring columns
+      // (sectors) and the same table entries are used together, in L2.
+      // About 16 items per block keep the tail short; an item keeps at
+      // least 16 units (each item restarts the block's copy pipeline).
       long long parts = (16ll * gridDim.x + batch - 1) / batch;
-      if (parts > ub) parts = ub;
+      if (parts > ub / 16) parts = ub / 16 > 0 ? ub / 16 : 1;  // at least 16 units per item
       const long long items = batch * parts;
       for (long long i = blockIdx.x; i < items; i += gridDim.x) {
         const long long b = i % batch, part = i / batch;
         __syncthreads();
-        pass_body<K, FTM>(A, reinterpret_cast<char*>(smem_raw_), b * ub + part * ub / parts, 1,
-                          b * ub + (part + 1) * ub / parts);
+        pass_body<K, FTM>(A, reinterpret_cast<char*>(smem_raw_), b * ub + part, parts, (b + 1) * ub);
       }
     } else {
       // one contiguous range of units per block (the tables fit in L2)
