@@ -330,7 +330,7 @@ turbofft_status turbofft_exec(turbofft_plan *plan, const void *in, void *out,
  * ordered after `stream`, and returns when `host_out` is complete.  Host
  * buffers should be pinned (cudaHostAlloc / cudaHostRegister) for full
  * bandwidth; pageable memory works but is slower.  The device staging (five
- * chunk buffers of about 64 MiB, or one transform if larger, and the
+ * chunk buffers of about 128 MiB, or one transform if larger, and the
  * streams) is shared by all plans of a device, allocated by the first call
  * and kept until the process exits; calls from several host threads on one
  * device are serialised.

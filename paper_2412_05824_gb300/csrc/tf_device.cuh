@@ -1442,9 +1442,16 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
       // once hold adjacent units of every transform: neighbouring columns
       // (sectors) and the same table entries are used together, in L2.
       // About 16 items per block keep the tail short; an item keeps at
-      // least 16 units (each item restarts the block's copy pipeline).
+      // least 16 units where it can (each item restarts the block's copy
+      // pipeline).
       long long parts = (16ll * gridDim.x + batch - 1) / batch;
-      if (parts > ub / 16) parts = ub / 16 > 0 ? ub / 16 : 1;  // at least 16 units per item
+      // items of at least 16 units, unless that leaves blocks without two
+      // items (few transforms: a chunk of a host-buffer exec)
+      const long long few = (2ll * gridDim.x + batch - 1) / batch;
+      const long long cap = ub / 16 > few ? ub / 16 : few;
+      if (parts > cap) parts = cap;
+      if (parts > ub) parts = ub;
+      if (parts < 1) parts = 1;
       const long long items = batch * parts;
       for (long long i = blockIdx.x; i < items; i += gridDim.x) {
         const long long b = i % batch, part = i / batch;

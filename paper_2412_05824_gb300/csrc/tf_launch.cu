@@ -198,7 +198,9 @@ void fill_cl_args(const turbofft_plan* p, const void* in, void* out, int64_t bat
 }
 
 // Device staging of turbofft_exec_host, shared by all plans of a device:
-// two input and two output chunk buffers plus a chunk-sized intermediate,
+// two input and two output chunk buffers (about 128 MiB each: enough
+// transforms per chunk to fill the GPU even at large N) plus a chunk-sized
+// intermediate,
 // three streams (copy in, transform, copy out) and their events.  Grown on
 // demand, kept until the process exits; one exec_host runs at a time per
 // device (the call is synchronous).
@@ -213,7 +215,7 @@ struct HostStage {
   bool ready = false;
 };
 HostStage g_stage[16];
-const size_t kStageChunkBytes = (size_t)64 << 20;
+const size_t kStageChunkBytes = (size_t)128 << 20;
 
 cudaError_t stage_reserve(HostStage& hs, size_t need) {
   cudaError_t e;

@@ -252,7 +252,7 @@ def test_float64_two_pass_checks_whole_transforms(n, batch):
 
 def test_float64_whole_transform_checks_through_host_chunks():
     """Host-buffer exec of a float64 two-pass plan runs in chunks of about
-    64 MiB (here 4 transforms of 16 MiB): every chunk starts its whole-
+    128 MiB (here 8 transforms of 16 MiB, two chunks): every chunk starts its whole-
     transform sums from zero, and a fault in a later chunk is corrected once,
     on its global transform index."""
     n, batch = 1 << 20, 11
