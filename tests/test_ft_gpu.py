@@ -272,3 +272,33 @@ def test_float64_whole_transform_checks_through_host_chunks():
     assert rep["detected"] == 1 and rep["corrected"] == 1 and rep["first_transform"] == 9, rep
     assert float(np.max(oracle.rel_l2(y.numpy(), ref))) <= tol
     plan.close()
+
+
+@pytest.mark.parametrize("direction", ["inverse", "inverse_unscaled", "forward_scaled"])
+def test_float64_whole_transform_checks_other_directions(direction):
+    """The whole-transform checks hold in the conjugated (inverse) domain and
+    before the output scaling: clean runs raise no alarm, a fault in either
+    pass is corrected."""
+    n, batch = 1 << 14, 6
+    x = ss.uniform_complex(15, batch, n, np.float64)
+    if direction == "forward_scaled":
+        ref = oracle.fft(x) / n
+    else:
+        ref = oracle.fft(x, inverse=True, scaled=direction == "inverse")
+    tol = oracle.tolerance(np.float64, n)
+    plan = tfl.Plan(n, batch, "complex128", direction, "correct")
+    assert plan.info()["transform_checks"] == 1
+    xd = torch.from_numpy(x).cuda()
+    y = plan.exec(xd).cpu().numpy()
+    rep = plan.report()
+    assert rep["detected"] == 0 and 0 < rep["max_clean_ratio"] < 0.8
+    assert float(np.max(oracle.rel_l2(y, ref))) <= tol
+    for p, st in ((0, 1), (1, 2)):
+        plan.inject(4, p, st, 999, 1, 45)
+        y = plan.exec(xd).cpu().numpy()
+        rep = plan.report()
+        assert rep["uncorrectable"] == 0
+        if rep["detected"]:
+            assert rep["corrected"] == 1 and rep["first_transform"] == 4
+        assert float(np.max(oracle.rel_l2(y, ref))) <= tol
+    plan.close()
