@@ -205,6 +205,69 @@ template <typename C> struct Dft<C, 2> {
 };
 
 // ---------------------------------------------------------------------------
+// float64 twiddled radix-R DFT (R = 2, 4, 8) as radix-2 decimation-in-time
+// layers whose twiddles are folded into the butterflies (Linzer and Feig,
+// "Modified FFTs for fused multiply-add architectures", Math. Comp. 1993):
+// a +- w b with w = c (1 + i t), |t| <= 1, costs 6 FMAs instead of 8 (a
+// complex product and two complex additions).  Where |Im w| > |Re w| the
+// factorisation is w = Im(w) (1 - i Re(w)/Im(w)) applied to i b; the
+// choice is carried in the lowest mantissa bit of the stored t (a change
+// of at most one ulp of t).  On GB300, whose float64 kernels are bound by
+// the FP64 pipe, this is 9 FP64 operations per value and radix-8 pass
+// instead of 10.5 (twiddle products, then the DFT).
+//
+// The pass twiddles of a thread, w = w_{LR}^{k m}, enter as the layer
+// twiddles (omega = w_{LR}^k, W_n = w_n):
+//   R = 8: omega^4, omega^2, W_4 omega^2, omega, W_4 omega, W_8 omega, W_8^3 omega
+//   R = 4: omega^2, omega, W_4 omega
+//   R = 2: omega
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void lf_bfly(double2& a, double2& b, double2 w) {
+  const bool sw = (__double2loint(w.y) & 1) != 0;
+  const double t = w.y, cc = w.x;
+  // b' = b, or i b = (-b.im, b.re) (sign by integer xor, off the FP64 pipe)
+  const double nbi = __longlong_as_double(__double_as_longlong(b.y) ^ (long long)0x8000000000000000ull);
+  const double pr = sw ? nbi : b.x;
+  const double pi = sw ? b.x : b.y;
+  const double u = fma(-t, pi, pr);
+  const double v = fma(t, pr, pi);
+  const double ar = a.x, ai = a.y;
+  a = make_double2(fma(cc, u, ar), fma(cc, v, ai));
+  b = make_double2(fma(-cc, u, ar), fma(-cc, v, ai));
+}
+template <int R> struct LfDft;
+template <> struct LfDft<2> {
+  static __device__ __forceinline__ void run(double2* x, const double2* w) { lf_bfly(x[0], x[1], w[0]); }
+};
+template <> struct LfDft<4> {
+  static __device__ __forceinline__ void run(double2* x, const double2* w) {
+    lf_bfly(x[0], x[2], w[0]);
+    lf_bfly(x[1], x[3], w[0]);
+    lf_bfly(x[0], x[1], w[1]);  // X0, X2
+    lf_bfly(x[2], x[3], w[2]);  // X1, X3
+    const double2 x1 = x[1];
+    x[1] = x[2];
+    x[2] = x1;
+  }
+};
+template <> struct LfDft<8> {
+  static __device__ __forceinline__ void run(double2* x, const double2* w) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) lf_bfly(x[m], x[m + 4], w[0]);  // p_m, q_m
+    lf_bfly(x[0], x[2], w[1]);                                  // P0+, P0-
+    lf_bfly(x[1], x[3], w[1]);                                  // P1+, P1-
+    lf_bfly(x[4], x[6], w[2]);                                  // Q0+, Q0-
+    lf_bfly(x[5], x[7], w[2]);                                  // Q1+, Q1-
+    lf_bfly(x[0], x[1], w[3]);                                  // X0, X4
+    lf_bfly(x[2], x[3], w[4]);                                  // X2, X6
+    lf_bfly(x[4], x[5], w[5]);                                  // X1, X5
+    lf_bfly(x[6], x[7], w[6]);                                  // X3, X7
+    const double2 y0 = x[0], y4 = x[1], y2 = x[2], y6 = x[3], y1 = x[4], y5 = x[5], y3 = x[6], y7 = x[7];
+    x[0] = y0; x[1] = y1; x[2] = y2; x[3] = y3; x[4] = y4; x[5] = y5; x[6] = y6; x[7] = y7;
+  }
+};
+
+// ---------------------------------------------------------------------------
 // compile-time configuration of one kernel
 // ---------------------------------------------------------------------------
 template <typename R_, int NS_, int E_, int S_, int KIND_>
@@ -351,9 +414,24 @@ template <class K, int BUDGET = 64> struct TwMode {
   static constexpr int MINB_FT = (MINB - TF_FT_MINB_DELTA) < 1 ? 1 : (MINB - TF_FT_MINB_DELTA);
 };
 
+// float64 kernels read the folded layer twiddles (c, t) of each pass from
+// one table: pass p (L > 1) holds L groups of R - 1 entries, k-major
+template <class K> constexpr bool lf_twiddles() { return std::is_same<typename K::real, double>::value; }
+template <class K, int p> struct LfOff {
+  static constexpr int v = LfOff<K, p - 1>::v + ((PassInfo<K, p - 1>::L > 1) ? PassInfo<K, p - 1>::L * (PassInfo<K, p - 1>::R - 1) : 0);
+};
+template <class K> struct LfOff<K, 0> { static constexpr int v = 0; };
+template <class K, int p> __device__ __forceinline__ int tw_index(int k, int m) {
+  using PI = PassInfo<K, p>;
+  if constexpr (lf_twiddles<K>()) return LfOff<K, p>::v + k * (PI::R - 1) + (m - 1);
+  else return PI::TWS * k * m;
+}
+
 template <class K, int BUDGET = 64> struct TwReg {
   using c = typename K::c;
   using M = TwMode<K, BUDGET>;
+  static_assert(!lf_twiddles<K>() || K::NP == 1 || K::E == 8,
+                "the float64 folded twiddle tables are laid out for radix-8 passes");
   c v[M::N];
   const c* __restrict__ tab;
   __device__ __forceinline__ void load(const c* __restrict__ tw, int t) {
@@ -366,7 +444,7 @@ template <class K, int BUDGET = 64> struct TwReg {
         for (int u = 0; u < PI::NB; ++u) {
           const int k = (t + u * K::P) & (PI::L - 1);
 #pragma unroll
-          for (int m = 1; m < PI::R; ++m) v[TwOff<K, p>::v + u * (PI::R - 1) + m - 1] = ldg(tw + PI::TWS * k * m);
+          for (int m = 1; m < PI::R; ++m) v[TwOff<K, p>::v + u * (PI::R - 1) + m - 1] = ldg(tw + tw_index<K, p>(k, m));
         }
       }
     });
@@ -374,7 +452,7 @@ template <class K, int BUDGET = 64> struct TwReg {
   template <int p> __device__ __forceinline__ c get(int u, int m, int k) const {
     using PI = PassInfo<K, p>;
     if constexpr (M::template reg<p>()) return v[TwOff<K, p>::v + u * (PI::R - 1) + m - 1];
-    else return ldg(tab + PI::TWS * k * m);
+    else return ldg(tab + tw_index<K, p>(k, m));
   }
 };
 
@@ -391,11 +469,18 @@ __device__ __forceinline__ void run_pass(typename K::c (&a)[K::E], typename K::c
     c b[R];
 #pragma unroll
     for (int m = 0; m < R; ++m) b[m] = a[u + m * NB];
-    if constexpr (L > 1) {
+    if constexpr (L > 1 && lf_twiddles<K>()) {
+      c w[R - 1];
 #pragma unroll
-      for (int m = 1; m < R; ++m) b[m] = cmul(b[m], tw.template get<p>(u, m, k));
+      for (int m = 1; m < R; ++m) w[m - 1] = tw.template get<p>(u, m, k);
+      LfDft<R>::run(b, w);
+    } else {
+      if constexpr (L > 1) {
+#pragma unroll
+        for (int m = 1; m < R; ++m) b[m] = cmul(b[m], tw.template get<p>(u, m, k));
+      }
+      Dft<c, R>::run(b);
     }
-    Dft<c, R>::run(b);
     if constexpr (PI::LAST) {
 #pragma unroll
       for (int m = 0; m < R; ++m) a[u + m * NB] = b[m];

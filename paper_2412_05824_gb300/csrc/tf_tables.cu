@@ -110,6 +110,61 @@ bool upload_pairs(turbofft_plan* p, void** dst, const std::vector<cld>& v) {
   return cudaMemcpy(*dst, t.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess;
 }
 
+// float64 pass twiddles folded into radix-2 layers, w = c (1 + i t)
+// (Linzer and Feig 1993): for each pass p > 0 of a sub-transform of ns
+// points done in radix-8 passes (the last one of radix ns / 8^(NP-1)), with
+// L = 8^p and omega = w_{L R}^k, k = 0 .. L-1, the R - 1 layer twiddles
+//   R = 8: omega^4, omega^2, W_4 omega^2, omega, W_4 omega, W_8 omega, W_8^3 omega
+//   R = 4: omega^2, omega, W_4 omega
+//   R = 2: omega
+// each stored as (c, t), c = Re w and t = Im w / Re w where |Re w| >= |Im w|,
+// else c = Im w and t = -Re w / Im w (then applied to i b); the lowest
+// mantissa bit of t says which (rounded to the nearer double with that bit).
+static std::vector<double> folded_twiddles(int ns) {
+  int lns = 0;
+  while ((1 << lns) < ns) ++lns;
+  const int np = (lns + 2) / 3;
+  std::vector<double> t;
+  auto put = [&](cld w) {
+    const ld wr = w.real(), wi = w.imag();
+    const bool sw = fabsl(wi) > fabsl(wr);
+    const ld c = sw ? wi : wr;
+    const ld tl = sw ? -wr / wi : wi / wr;
+    double td = (double)tl;
+    uint64_t bits;
+    memcpy(&bits, &td, 8);
+    if ((bits & 1u) != (uint64_t)sw) td = nextafter(td, ((ld)td < tl) ? (double)INFINITY : -(double)INFINITY);
+    if (td == 0.0 && sw) td = nextafter(0.0, 1.0);  // +-0 carries no set bit
+    t.push_back((double)c);
+    t.push_back(td);
+  };
+  for (int q = 1; q < np; ++q) {
+    const int lr = (q == np - 1) ? lns - 3 * (np - 1) : 3;
+    const int r = 1 << lr;
+    const int64_t l = (int64_t)1 << (3 * q);
+    const int64_t n = l * r;  // omega = w_n^k; W_4 = w_n^(n/4), W_8 = w_n^(n/8)
+    for (int64_t k = 0; k < l; ++k) {
+      if (r == 8) {
+        put(root(n, 4 * k));
+        put(root(n, 2 * k));
+        put(root(n, 2 * k + n / 4));
+        put(root(n, k));
+        put(root(n, k + n / 4));
+        put(root(n, k + n / 8));
+        put(root(n, k + 3 * n / 8));
+      } else if (r == 4) {
+        put(root(n, 2 * k));
+        put(root(n, k));
+        put(root(n, k + n / 4));
+      } else {
+        put(root(n, k));
+      }
+    }
+  }
+  if (t.empty()) t.assign(2, 0.0);  // one pass: no twiddles are read
+  return t;
+}
+
 bool upload_tables(turbofft_plan* p, PassPlan& pp) {
   const int ns = pp.ns;
   std::vector<cld> tw(ns);
@@ -135,7 +190,10 @@ bool upload_tables(turbofft_plan* p, PassPlan& pp) {
 #endif
     return ok;
   }
-  return upload<double>(p, &pp.d_tw, tw) && upload<double>(p, &pp.d_ev, e) && upload<double>(p, &pp.d_vv, v);
+  const std::vector<double> lf = folded_twiddles(ns);
+  return dev_alloc(p, &pp.d_tw, lf.size() * sizeof(double)) &&
+         cudaMemcpy(pp.d_tw, lf.data(), lf.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
+         upload<double>(p, &pp.d_ev, e) && upload<double>(p, &pp.d_vv, v);
 }
 
 namespace {
