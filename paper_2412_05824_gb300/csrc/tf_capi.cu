@@ -69,6 +69,7 @@ void fill_info(const turbofft_plan* p, turbofft_plan_info* info) {
   }
   info->num_passes = p->num_passes;
   info->transform_checks = p->tchk ? 1 : 0;
+  info->tma_columns = p->tma ? 1 : 0;
   if (p->cl) {
     const ClEntry* ce = p->cl;
     info->cluster = ce->cluster;
@@ -309,6 +310,31 @@ turbofft_status create_plan(int64_t n, int64_t batch, turbofft_dtype dtype, int 
       return TURBOFFT_ALLOC_FAILED;
     }
   }
+  // float32 two-pass plans stage the column pass's tiles with TMA: always
+  // (mode 2) or where it measured faster than cp.async on GB300 (mode 1:
+  // tile rows of 64 bytes or more, and N1 >= 1024 or checksums on; rows of
+  // 16-32 bytes ran 1-24% slower); the kernels' timeout flag
+  {
+    const int mode = g_column_tma.load();
+    const KernelEntry* ke0 = p->pass[0].ke;
+    const bool can = dt == 0 && p->num_passes == 2 && !p->cl && !t_ragged_member && ke0 &&
+                     ke0->main_tma[0] != nullptr;
+    const bool faster = ke0 && ke0->s * 8 >= 64 && (ke0->ns >= 1024 || ft_mode != TURBOFFT_FT_OFF);
+    p->tma = can && (mode == 2 || (mode == 1 && faster));
+  }
+  if (p->tma) {
+    if (p->d_fts) {
+      p->d_err = &p->d_fts->error;
+    } else {
+      void* e = nullptr;
+      if (!dev_alloc(p, &e, 16) || cudaMemset(e, 0, 16) != cudaSuccess) {
+        cudaGetLastError();
+        turbofft_destroy(p);
+        return TURBOFFT_ALLOC_FAILED;
+      }
+      p->d_err = static_cast<int*>(e);
+    }
+  }
   if (cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     turbofft_destroy(p);
@@ -422,6 +448,12 @@ turbofft_status turbofft_plan_create(int64_t n, int64_t batch, turbofft_dtype dt
 turbofft_status turbofft_plan_get_info(const turbofft_plan* p, turbofft_plan_info* info) {
   if (!p || !info) return TURBOFFT_INVALID_VALUE;
   fill_info(p, info);
+  return TURBOFFT_SUCCESS;
+}
+
+turbofft_status turbofft_set_column_tma(int mode) {
+  if (mode < 0 || mode > 2) return TURBOFFT_INVALID_VALUE;
+  g_column_tma.store(mode);
   return TURBOFFT_SUCCESS;
 }
 
@@ -549,6 +581,21 @@ turbofft_status turbofft_get_report(turbofft_plan* p, turbofft_report* r) {
     if (e != cudaSuccess) return cuda_fail(p, e, "report wait");
     if (rg_timed_out(p)) {
       p->last_error = "ragged persistent kernel: grid barrier timed out";
+      return TURBOFFT_TIMEOUT;
+    }
+  }
+  if (p->tma && p->have_exec) {
+    // TMA-staged column pass: a tile copy that never completed
+    cudaError_t e = cudaEventSynchronize(p->done);
+    if (e != cudaSuccess) return cuda_fail(p, e, "report wait");
+    int err = 0;
+    if (p->ft_mode != TURBOFFT_FT_OFF) {
+      err = p->h_fts->error;
+    } else if ((e = cudaMemcpy(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess) {
+      return cuda_fail(p, e, "report read");
+    }
+    if (err) {
+      p->last_error = "column pass: a TMA tile copy did not complete in time";
       return TURBOFFT_TIMEOUT;
     }
   }

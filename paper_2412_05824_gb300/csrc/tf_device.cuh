@@ -36,6 +36,7 @@
 //   correction, Sec. 4.1.2).
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the tensor-map type of TMA copies)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -702,6 +703,7 @@ template <typename R> struct PassArgs {
   void* rec_sums; // MAX_RECORDS x 2 x NS_MAX complex (x_bar, y_bar)
   int rec_stride; // complex elements per record half (NS_MAX)
   InjectSite inj;
+  int* err;       // TMA-staged passes: set to 1 when a bounded wait expires
 };
 
 // column n2 of a column-pass signal (within its transform)
@@ -838,6 +840,57 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// tensor-memory-accelerator (TMA) tile loads completing on an mbarrier
+// (float32 column passes: a column tile is one 2-D box of S columns x up to
+// 256 rows of the input viewed as [rows][n2] complex values)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* mb, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(mb)), "r"(count) : "memory");
+}
+// make the initialised barriers visible to the asynchronous (TMA) proxy
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// order this thread's earlier (barrier-synchronised) shared-memory accesses
+// before the asynchronous proxy's writes of the next TMA copy
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* mb, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(mb)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* mb, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done)
+      : "r"(smem_addr(mb)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// bounded wait for phase `parity` of an mbarrier: false after about 2^22
+// polls (each try_wait may itself suspend the thread for a while)
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* mb, unsigned parity) {
+  for (int i = 0; i < (1 << 22); ++i)
+    if (mbar_try_wait(mb, parity)) return true;
+  return false;
+}
+// 2-D tile load: box at element coordinates (x, y) of the tensor map into
+// shared memory at dst (128-byte aligned), completion counted on mb
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y,
+                                            unsigned long long* mb) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];\n" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<unsigned long long>(tm)), "r"(x), "r"(y), "r"(smem_addr(mb))
+      : "memory");
+}
+
 // Staged tiles of slot-major (SP, ROW) kernels keep each slot's positions
 // XOR-swizzled by (slot % M) * P, in whole 16-byte chunks: when a slot's P
 // threads read fewer than 128 bytes per register index, the M slots of one
@@ -946,6 +999,34 @@ __device__ __forceinline__ void issue_unit(const PassArgs<typename K::real>& A, 
   }
 }
 
+// float32 column passes may stage their tiles with TMA: the tile of S
+// columns (S x 8 bytes, a multiple of 16) and NS rows is dense in shared
+// memory in the order the cp.async path writes it
+template <class K> constexpr bool tma_ok() {
+  return K::KIND == KIND_COL && std::is_same<typename K::real, float>::value && (K::S * 8) % 16 == 0 &&
+         K::S <= 256 && (stage_bytes<K>() % 128) == 0;
+}
+template <class K> constexpr int tma_box_rows() { return K::NS < 256 ? K::NS : 256; }
+// Issue the TMA copies of column-pass unit `unit`'s tile (one thread): the
+// input is viewed as rows of n2 values, row b * (n / n2) + p holding row p
+// of transform b's column tile; c0 (a multiple of S, so c0 * 8 bytes is a
+// multiple of 16) is the first column
+template <class K>
+__device__ __forceinline__ void issue_unit_tma(const PassArgs<typename K::real>& A, const CUtensorMap* tm,
+                                               long long unit, char* stage, unsigned long long* mb) {
+  long long b;
+  int c0;
+  col_unit<K>(A.geo, unit, b, c0);
+  constexpr int BR = tma_box_rows<K>();
+  constexpr unsigned bytes = (unsigned)(K::NS * K::S * sizeof(typename K::c));
+  const int row0 = (int)(b * (A.geo.n / A.geo.n2));
+  fence_proxy_async_smem();
+  mbar_arrive_expect_tx(mb, bytes);
+#pragma unroll
+  for (int r = 0; r < K::NS / BR; ++r)
+    tma_load_2d(stage + (size_t)r * BR * K::S * sizeof(typename K::c), tm, c0, row0 + r * BR, mb);
+}
+
 __device__ __forceinline__ void atomic_max_nonneg(float* addr, float v) {
   atomicMax(reinterpret_cast<int*>(addr), __float_as_int(v));
 }
@@ -975,10 +1056,13 @@ template <class K> __device__ __forceinline__ long long unit_transform(const Geo
 // stride, ... below end (the pass kernel: blockIdx.x, gridDim.x, all units;
 // the persistent ragged kernel: a contiguous range per work item).  The
 // caller makes sure that no thread of the block still uses shared memory of
-// an earlier call.
-template <class K, int FTM>
+// an earlier call.  TMA: tiles are staged by TMA copies described by the
+// tensor map `tm` (float32 column passes of two-pass plans); a block whose
+// wait for a tile runs out records TURBOFFT_TIMEOUT in the plan's state and
+// stops.
+template <class K, int FTM, bool TMA = false>
 __device__ __forceinline__ void pass_body(const PassArgs<typename K::real>& A, char* smem_raw, long long first,
-                                          long long stride, long long end) {
+                                          long long stride, long long end, const CUtensorMap* tm = nullptr) {
   using R = typename K::real;
   using c = typename K::c;
   constexpr int E = K::E, P = K::P, S = K::S;
@@ -1043,18 +1127,50 @@ __device__ __forceinline__ void pass_body(const PassArgs<typename K::real>& A, c
     for (int i = 0; i < E; ++i) { xs[i] = mk<c>(0, 0); ys[i] = mk<c>(0, 0); }
   }
 
+  static_assert(!TMA || tma_ok<K>(), "TMA staging: float32 column passes");
+  __shared__ __align__(8) unsigned long long tma_mb[TMA ? NSTAGE : 1];
+  __shared__ int tma_fail;
+  if constexpr (TMA) {
+    if (tid == 0) {
+#pragma unroll
+      for (int k = 0; k < NSTAGE; ++k) mbar_init(&tma_mb[k], 1);
+      mbar_init_fence();
+      tma_fail = 0;
+    }
+    __syncthreads();
+  }
   // prologue: the first NSTAGE-1 transactions' tiles in flight
 #pragma unroll
   for (int k = 0; k < NSTAGE - 1; ++k) {
     const long long u = first + k * stride;
-    if (u < end) issue_unit<K>(A, u, smem_raw + k * stage_bytes<K>(), tid);
-    cp_async_commit();
+    if constexpr (TMA) {
+      if (u < end && tid == 0) issue_unit_tma<K>(A, tm, u, smem_raw + k * stage_bytes<K>(), &tma_mb[k]);
+    } else {
+      if (u < end) issue_unit<K>(A, u, smem_raw + k * stage_bytes<K>(), tid);
+      cp_async_commit();
+    }
   }
   int it = 0;
   for (long long unit = first; unit < end; unit += stride, ++it) {
     // prefetch NSTAGE-1 transactions ahead into the stage freed by the
     // previous transaction, then wait for this transaction's tile
-    {
+    if constexpr (TMA) {
+      const long long un = unit + (NSTAGE - 1) * stride;
+      const int sn = (it + NSTAGE - 1) % NSTAGE;
+      if (un < end && tid == 0) issue_unit_tma<K>(A, tm, un, smem_raw + sn * stage_bytes<K>(), &tma_mb[sn]);
+      // the stage of transaction `it` completes its (it / NSTAGE)-th phase
+      if (!mbar_wait_bounded(&tma_mb[it % NSTAGE], (unsigned)(it / NSTAGE) & 1u)) tma_fail = 1;
+      __syncthreads();
+      if (tma_fail) {
+        // a copy that never completed: record the timeout, give the copy
+        // just issued a bounded wait, and stop this block
+        if (tid == 0) {
+          if (A.err) atomicExch(A.err, 1);
+          if (un < end) mbar_wait_bounded(&tma_mb[sn], (unsigned)((it + NSTAGE - 1) / NSTAGE) & 1u);
+        }
+        return;
+      }
+    } else {
       const long long un = unit + (NSTAGE - 1) * stride;
       if (un < end) issue_unit<K>(A, un, smem_raw + ((it + NSTAGE - 1) % NSTAGE) * stage_bytes<K>(), tid);
       cp_async_commit();
@@ -1553,6 +1669,22 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
   } else {
     pass_body<K, FTM>(A, reinterpret_cast<char*>(smem_raw_), blockIdx.x, gridDim.x, A.num_units);
   }
+}
+
+// The pass kernel with TMA-staged tiles (float32 column passes).  The tensor
+// map is a kernel parameter (__grid_constant__: TMA reads it in place).  The
+// launch adds 128 bytes of dynamic shared memory so that the ring can start
+// on a 128-byte boundary, as TMA destinations must.
+template <class K> constexpr int tma_smem_bytes(int ftm) {
+  return (ftm ? pass_smem_bytes<K, 1>() : pass_smem_bytes<K, 0>()) + 128;
+}
+template <class K, int FTM>
+__global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_FT : TwMode<K>::MINB)
+    tf_pass_kernel_tma(const PassArgs<typename K::real> A, const __grid_constant__ CUtensorMap tm) {
+  extern __shared__ __align__(128) unsigned char smem_raw_[];
+  const unsigned mis = smem_addr(smem_raw_) & 127u;
+  char* const ring = reinterpret_cast<char*>(smem_raw_) + (mis ? 128u - mis : 0u);
+  pass_body<K, FTM, true>(A, ring, blockIdx.x, gridDim.x, A.num_units, &tm);
 }
 
 // Transform-level correction (float64 two-pass plans): the transforms the

@@ -10,6 +10,26 @@ template <class K, int FTM> void launch_main(const void* a, int grid, cudaStream
   tf_pass_kernel<K, FTM><<<grid, K::NT, pass_smem_bytes<K, FTM>(), s>>>(
       *static_cast<const PassArgs<typename K::real>*>(a));
 }
+template <class K, int FTM> void launch_main_tma(const void* a, const void* tm, int grid, cudaStream_t s) {
+  tf_pass_kernel_tma<K, FTM><<<grid, K::NT, tma_smem_bytes<K>(FTM), s>>>(
+      *static_cast<const PassArgs<typename K::real>*>(a), *static_cast<const CUtensorMap*>(tm));
+}
+template <class K> void set_tma(KernelEntry& e) {
+  if constexpr (tma_ok<K>()) {
+    e.smem_tma[0] = tma_smem_bytes<K>(0);
+    e.smem_tma[1] = tma_smem_bytes<K>(1);
+    e.main_tma[0] = &launch_main_tma<K, 0>;
+    e.main_tma[1] = &launch_main_tma<K, 1>;
+    e.fn_main_tma[0] = reinterpret_cast<const void*>(&tf_pass_kernel_tma<K, 0>);
+    e.fn_main_tma[1] = reinterpret_cast<const void*>(&tf_pass_kernel_tma<K, 1>);
+  } else {
+    for (int v = 0; v < 2; ++v) {
+      e.smem_tma[v] = 0;
+      e.main_tma[v] = nullptr;
+      e.fn_main_tma[v] = nullptr;
+    }
+  }
+}
 template <class K> void launch_fix(const void* a, int grid, cudaStream_t s) {
   tf_fix_kernel<K><<<grid, K::NT, K::SMEM_BYTES, s>>>(*static_cast<const PassArgs<typename K::real>*>(a));
 }
@@ -65,6 +85,7 @@ template <class K> KernelEntry make_entry() {
     e.tcfix = nullptr;
     e.fn_tcfix = nullptr;
   }
+  set_tma<K>(e);
   return e;
 }
 
@@ -91,6 +112,11 @@ template <class K> KernelEntry make_entry_plain() {
   e.smem_fix = 0;
   e.fix = nullptr;
   e.fn_fix = nullptr;
+  for (int v = 0; v < 2; ++v) {
+    e.smem_tma[v] = 0;
+    e.main_tma[v] = nullptr;
+    e.fn_main_tma[v] = nullptr;
+  }
   return e;
 }
 

@@ -1,6 +1,8 @@
 // Kernel launches of an exec: per-pass arguments, the pass sequence with its
 // correction kernels, the exec helpers shared by every entry point, and the
 // host-buffer exec with its pipelined staging.
+#include <cuda.h>
+#include <cudaTypedefs.h>  // PFN_cuTensorMapEncodeTiled
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -60,7 +62,52 @@ bool set_smem_attrs(const KernelEntry* ke) {
   if (ke->fn_tcfix && cudaFuncSetAttribute(ke->fn_tcfix, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            ke->smem_main[0]) != cudaSuccess)
     return false;
+  for (int v = 0; v < 2; ++v)
+    if (ke->fn_main_tma[v] && cudaFuncSetAttribute(ke->fn_main_tma[v], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   ke->smem_tma[v]) != cudaSuccess)
+      return false;
   return true;
+}
+
+std::atomic<int> g_column_tma{1};
+
+namespace {
+// the driver's tensor-map encoder, looked up once through the runtime
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      f = nullptr;
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  return fn;
+}
+}  // namespace
+
+// Tensor map of a float32 two-pass plan's column-pass input `in` (batch
+// transforms): the input viewed as rows of n2 complex values (8-byte
+// elements), boxes of S columns x min(N1, 256) rows.  False where TMA cannot
+// describe it (input not 16-byte aligned, 2^31 rows or more, no encoder):
+// the exec then stages with cp.async.
+bool encode_column_map(const turbofft_plan* p, const void* in, int64_t batch, CUtensorMap* m) {
+  const PassPlan& pp = p->pass[0];
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || ((uintptr_t)in & 15u) != 0 || pp.kind != tf::KIND_COL) return false;
+  const uint64_t n2 = (uint64_t)pp.g_n2;
+  const uint64_t rows = (uint64_t)batch * (uint64_t)pp.bm * ((uint64_t)pp.g_n / n2);
+  if (rows == 0 || rows >= (1ull << 31) || (n2 * 8) % 16 != 0) return false;
+  const cuuint64_t dims[2] = {n2, rows};
+  const cuuint64_t strides[1] = {n2 * 8};
+  const cuuint32_t box[2] = {(cuuint32_t)pp.ke->s, (cuuint32_t)std::min(pp.ke->ns, 256)};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void*>(in), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 long long units_for(const turbofft_plan* p, int pi, int64_t batch) {
@@ -170,6 +217,7 @@ void fill_args(const turbofft_plan* p, int pi, const void* in, void* out, int64_
   A.rec_sums = p->d_rec_sums;
   A.rec_stride = p->rec_stride;
   A.inj = inj;
+  A.err = p->d_err;
 }
 
 }  // namespace
@@ -283,7 +331,17 @@ turbofft_status run(turbofft_plan* p, const void* in, void* out, void* scratch, 
     if (p->dtype == TURBOFFT_C2C_F32) {
       tf::PassArgs<float> A;
       fill_args<float>(p, pi, pin, pout, batch, tbase, inj, A);
-      timed(2 * pi, [&] { pp.ke->main[ft_variant(p->ft_mode)](&A, grid, stream); });
+      const int v = ft_variant(p->ft_mode);
+      // the column pass of a two-pass plan: tiles staged by TMA where it can
+      CUtensorMap tm;
+      const bool tma = pi == 0 && p->tma && p->num_passes == 2 && p->d_tab == nullptr && v <= 1 &&
+                       pp.ke->main_tma[v] && encode_column_map(p, pin, batch, &tm);
+      timed(2 * pi, [&] {
+        if (tma)
+          pp.ke->main_tma[v](&A, &tm, grid, stream);
+        else
+          pp.ke->main[v](&A, grid, stream);
+      });
       if (ft) timed(2 * pi + 1, [&] { pp.ke->fix(&A, 8, stream); });
     } else if (p->pairs) {
       tf::PassArgs<tf::dd> A;  // no checksums: no correction kernel

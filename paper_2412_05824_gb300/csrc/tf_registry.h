@@ -6,6 +6,8 @@
 namespace tf {
 
 typedef void (*LaunchFn)(const void* args, int grid, cudaStream_t stream);
+// pass kernel with TMA-staged tiles: args as LaunchFn, tmap a CUtensorMap
+typedef void (*LaunchTmaFn)(const void* args, const void* tmap, int grid, cudaStream_t stream);
 
 struct KernelEntry {
   int dtype;        // 0 float, 1 double, 2 double data in float-pair arithmetic
@@ -26,6 +28,11 @@ struct KernelEntry {
   const void* fn_main[5];
   const void* fn_fix;
   const void* fn_tcfix;
+  // float32 column passes: the transform kernel with TMA-staged tiles, no
+  // checksums / checksums (null otherwise)
+  int smem_tma[2];
+  LaunchTmaFn main_tma[2];
+  const void* fn_main_tma[2];
 };
 
 // all entries of one translation unit

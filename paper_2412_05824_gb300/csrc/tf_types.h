@@ -56,7 +56,7 @@ struct FtState {
   unsigned long long dropped;       // detections beyond MAX_RECORDS (counted uncorrectable)
   unsigned long long num_records;
   float max_clean_ratio;
-  int pad;
+  int error;  // nonzero: a bounded device wait of an exec expired (TURBOFFT_TIMEOUT)
   FtRecord rec[MAX_RECORDS];
 };
 

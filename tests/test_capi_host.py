@@ -183,3 +183,28 @@ def test_thread_level_mode_rejected_where_it_cannot_apply(L):
     assert L.turbofft_plan_create_structured(1 << 14, 4, 0, -1, 4, 2, ctypes.byref(h)) == tfl.UNSUPPORTED
     assert L.turbofft_plan_create_structured(1 << 22, 1, 0, -1, 4, 3, ctypes.byref(h)) == tfl.UNSUPPORTED
     assert L.turbofft_plan_create(64, 4, 0, -1, 5, ctypes.byref(h)) == tfl.INVALID_VALUE
+
+
+def test_process_wide_switches_need_no_device(L):
+    """The staging / launch-form switches only record a choice for plans
+    created afterwards."""
+    for f in (L.turbofft_set_column_tma, L.turbofft_set_ragged_single_launch):
+        assert f(0) == tfl.SUCCESS
+        assert f(1) == tfl.SUCCESS
+    assert L.turbofft_set_column_tma(2) == tfl.SUCCESS
+    assert L.turbofft_set_column_tma(3) == tfl.INVALID_VALUE
+    assert L.turbofft_set_column_tma(-1) == tfl.INVALID_VALUE
+    assert L.turbofft_set_column_tma(1) == tfl.SUCCESS
+
+
+def test_plan_info_layout_matches_header():
+    """The binding's PlanInfo mirrors the header's field list."""
+    src = open(HEADER).read()
+    body = src[src.index("/* Static facts about a plan. */"):src.index("} turbofft_plan_info;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = re.findall(r"\b(?:int32_t|int64_t)\s+([^;]+);", body)
+    fields = []
+    for decl in names:
+        for part in decl.split(","):
+            fields.append(re.sub(r"\[.*\]", "", part).strip())
+    assert fields == [name for name, _ in tfl.PlanInfo._fields_]
