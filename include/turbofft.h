@@ -172,9 +172,8 @@ typedef struct {
   int32_t transform_checks; /* 1: checksums over whole transforms (F64 two-pass plans with
                                DETECT / CORRECT): an exec launches the two passes, a check
                                kernel and two recompute kernels */
-  int32_t tma_columns;      /* 1: F32 two-pass plan whose column pass stages its input tiles with
-                               TMA tensor copies (turbofft_set_column_tma); 0: 16-byte cp.async
-                               copies */
+  int32_t tma_passes;       /* bit p set: pass p stages its input tiles with TMA copies
+                               (turbofft_set_tma_staging); else 16-byte cp.async copies */
 } turbofft_plan_info;
 
 /* Duration of one kernel of the last exec (turbofft_set_profiling). */
@@ -313,23 +312,28 @@ turbofft_status turbofft_set_autotune(int enable);
 turbofft_status turbofft_set_ragged_single_launch(int enable);
 
 /*
- * Process-wide: how F32 two-pass plans created afterwards stage the column
- * pass's input tiles: mode 0 with 16-byte cp.async copies; 1 (the default)
- * with TMA (tensor-memory-accelerator) copies where they measured faster on
- * GB300 (tile rows of S x 8 >= 64 bytes, and N1 >= 1024 or ft_mode not OFF),
- * else cp.async; 2 with TMA wherever the shape allows.  A column tile (S
- * adjacent columns of the N1 x N2 view, Sec. 3.1's kernel-level tiling) is
- * one 2-D box of the input viewed as rows of N2 values; one thread issues
- * it, completion is counted on a shared-memory barrier.  The results are
- * bitwise the same either way.  Each exec encodes the tensor map
- * of its input pointer (16-byte aligned, as every exec requires); an input
- * viewed as 2^31 rows or more runs that exec with cp.async.  The wait for a tile is
- * bounded: after about a second without completion the kernel stops and
- * turbofft_get_report returns TURBOFFT_TIMEOUT (for plans with ft_mode OFF
- * that flag then stays set for the plan).  Returns SUCCESS, or
+ * Process-wide: how F32 one- and two-pass plans created afterwards stage
+ * their input tiles: mode 0 with 16-byte cp.async copies by every thread; 1
+ * (the default) with TMA (tensor-memory-accelerator) copies issued by one
+ * thread where they measured faster on GB300 (row passes; column passes
+ * whose tile rows are S x 8 >= 64 bytes, at N1 >= 512 or with ft_mode not
+ * OFF; single passes of N = 4096, of 1024 and 2048 with ft_mode not OFF,
+ * of 256 and 8192 with ft_mode OFF), else cp.async; 2 with TMA wherever the
+ * kernel's tile allows it.  A column tile
+ * (S adjacent columns of the N1 x N2 view, Sec. 3.1's kernel-level tiling)
+ * is one 2-D box of the input viewed as rows of N2 values; the tile of a
+ * single pass (S whole transforms) or of a row pass (S adjacent rows) is one
+ * contiguous bulk copy where the kernel keeps it unswizzled in shared memory.
+ * Completion is counted on a shared-memory barrier.  The results are
+ * bitwise the same either way.  Each exec encodes the tensor map of a column
+ * pass's input pointer (16-byte aligned, as every exec requires); an input
+ * viewed as 2^31 rows or more runs that exec with cp.async.  The wait for a
+ * tile is bounded: after about a second without completion the kernel stops
+ * and turbofft_get_report returns TURBOFFT_TIMEOUT (for plans with ft_mode
+ * OFF that flag then stays set for the plan).  Returns SUCCESS, or
  * INVALID_VALUE for a mode outside 0..2.
  */
-turbofft_status turbofft_set_column_tma(int mode);
+turbofft_status turbofft_set_tma_staging(int mode);
 
 /*
  * Transform `in` into `out` (both device pointers, see the layout above) on

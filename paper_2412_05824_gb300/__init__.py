@@ -78,7 +78,7 @@ class PlanInfo(ctypes.Structure):
                 ("scratch_bytes", ctypes.c_int64), ("per_block", ctypes.c_int32 * 3),
                 ("num_members", ctypes.c_int32), ("autotuned", ctypes.c_int32),
                 ("cluster", ctypes.c_int32), ("single_launch", ctypes.c_int32),
-                ("transform_checks", ctypes.c_int32), ("tma_columns", ctypes.c_int32)]
+                ("transform_checks", ctypes.c_int32), ("tma_passes", ctypes.c_int32)]
 
 
 class KernelTime(ctypes.Structure):
@@ -92,7 +92,7 @@ EXPORTS = [
     "turbofft_set_workspace", "turbofft_set_profiling", "turbofft_get_kernel_times",
     "turbofft_exec_static_scratch", "turbofft_plan_create_ragged", "turbofft_plan_get_member_info",
     "turbofft_set_autotune", "turbofft_plan_create_structured", "turbofft_set_group_transactions",
-    "turbofft_fma_peak", "turbofft_set_ragged_single_launch", "turbofft_set_column_tma",
+    "turbofft_fma_peak", "turbofft_set_ragged_single_launch", "turbofft_set_tma_staging",
 ]
 
 _lib = None
@@ -116,7 +116,7 @@ def lib() -> ctypes.CDLL:
     L.turbofft_plan_get_member_info.argtypes = [vp, i32, ctypes.POINTER(PlanInfo)]
     L.turbofft_set_autotune.argtypes = [i32]
     L.turbofft_set_ragged_single_launch.argtypes = [i32]
-    L.turbofft_set_column_tma.argtypes = [i32]
+    L.turbofft_set_tma_staging.argtypes = [i32]
     L.turbofft_set_group_transactions.argtypes = [vp, i32]
     L.turbofft_plan_create_structured.argtypes = [i64, i64, i32, i32, i32, i32, ctypes.POINTER(vp)]
     L.turbofft_inject.argtypes = [vp, Site, i32]
@@ -320,13 +320,13 @@ def set_ragged_single_launch(enable: bool = True):
     _check(lib().turbofft_set_ragged_single_launch(1 if enable else 0), "turbofft_set_ragged_single_launch")
 
 
-def set_column_tma(mode="auto"):
-    """Process-wide: how float32 two-pass plans created afterwards stage
-    their column-pass tiles (turbofft_set_column_tma): "auto" (TMA tensor
-    copies where they measured faster, else cp.async), "always" (TMA
-    wherever the shape allows) or "never" (16-byte cp.async copies)."""
+def set_tma_staging(mode="auto"):
+    """Process-wide: how float32 one- and two-pass plans created afterwards
+    stage their input tiles (turbofft_set_tma_staging): "auto" (TMA copies
+    where they measured faster, else cp.async), "always" (TMA wherever the
+    kernel's tile allows it) or "never" (16-byte cp.async copies)."""
     modes = {"never": 0, "auto": 1, "always": 2}
-    _check(lib().turbofft_set_column_tma(modes[mode]), "turbofft_set_column_tma")
+    _check(lib().turbofft_set_tma_staging(modes[mode]), "turbofft_set_tma_staging")
 
 
 def packed_offsets(sizes, dtype="complex64"):

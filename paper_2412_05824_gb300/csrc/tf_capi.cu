@@ -69,7 +69,7 @@ void fill_info(const turbofft_plan* p, turbofft_plan_info* info) {
   }
   info->num_passes = p->num_passes;
   info->transform_checks = p->tchk ? 1 : 0;
-  info->tma_columns = p->tma ? 1 : 0;
+  info->tma_passes = p->tma_mask;
   if (p->cl) {
     const ClEntry* ce = p->cl;
     info->cluster = ce->cluster;
@@ -310,19 +310,19 @@ turbofft_status create_plan(int64_t n, int64_t batch, turbofft_dtype dtype, int 
       return TURBOFFT_ALLOC_FAILED;
     }
   }
-  // float32 two-pass plans stage the column pass's tiles with TMA: always
-  // (mode 2) or where it measured faster than cp.async on GB300 (mode 1:
-  // tile rows of 64 bytes or more, and N1 >= 1024 or checksums on; rows of
-  // 16-32 bytes ran 1-24% slower); the kernels' timeout flag
-  {
-    const int mode = g_column_tma.load();
-    const KernelEntry* ke0 = p->pass[0].ke;
-    const bool can = dt == 0 && p->num_passes == 2 && !p->cl && !t_ragged_member && ke0 &&
-                     ke0->main_tma[0] != nullptr;
-    const bool faster = ke0 && ke0->s * 8 >= 64 && (ke0->ns >= 1024 || ft_mode != TURBOFFT_FT_OFF);
-    p->tma = can && (mode == 2 || (mode == 1 && faster));
+  // float32 one- and two-pass plans may stage their tiles with TMA copies:
+  // always (mode 2) or where that measured faster than cp.async on GB300
+  // (mode 1, tma_faster); the kernels' timeout flag
+  p->tma_mask = 0;
+  if (dt == 0 && p->num_passes <= 2 && !p->cl && !t_ragged_member) {
+    const int mode = g_tma_staging.load();
+    for (int pi = 0; pi < p->num_passes; ++pi) {
+      const KernelEntry* ke = p->pass[pi].ke;
+      if (ke && ke->main_tma[0] && (mode == 2 || (mode == 1 && tma_faster(ke, ft_mode))))
+        p->tma_mask |= 1 << pi;
+    }
   }
-  if (p->tma) {
+  if (p->tma_mask) {
     if (p->d_fts) {
       p->d_err = &p->d_fts->error;
     } else {
@@ -451,9 +451,9 @@ turbofft_status turbofft_plan_get_info(const turbofft_plan* p, turbofft_plan_inf
   return TURBOFFT_SUCCESS;
 }
 
-turbofft_status turbofft_set_column_tma(int mode) {
+turbofft_status turbofft_set_tma_staging(int mode) {
   if (mode < 0 || mode > 2) return TURBOFFT_INVALID_VALUE;
-  g_column_tma.store(mode);
+  g_tma_staging.store(mode);
   return TURBOFFT_SUCCESS;
 }
 
@@ -584,8 +584,8 @@ turbofft_status turbofft_get_report(turbofft_plan* p, turbofft_report* r) {
       return TURBOFFT_TIMEOUT;
     }
   }
-  if (p->tma && p->have_exec) {
-    // TMA-staged column pass: a tile copy that never completed
+  if (p->tma_mask && p->have_exec) {
+    // TMA-staged pass: a tile copy that never completed
     cudaError_t e = cudaEventSynchronize(p->done);
     if (e != cudaSuccess) return cuda_fail(p, e, "report wait");
     int err = 0;
@@ -595,7 +595,7 @@ turbofft_status turbofft_get_report(turbofft_plan* p, turbofft_report* r) {
       return cuda_fail(p, e, "report read");
     }
     if (err) {
-      p->last_error = "column pass: a TMA tile copy did not complete in time";
+      p->last_error = "a TMA tile copy did not complete in time";
       return TURBOFFT_TIMEOUT;
     }
   }

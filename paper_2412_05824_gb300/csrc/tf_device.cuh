@@ -843,7 +843,8 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
 // ---------------------------------------------------------------------------
 // tensor-memory-accelerator (TMA) tile loads completing on an mbarrier
 // (float32 column passes: a column tile is one 2-D box of S columns x up to
-// 256 rows of the input viewed as [rows][n2] complex values)
+// 256 rows of the input viewed as [rows][n2] complex values; row passes and
+// single-pass transforms with an unswizzled tile: one contiguous bulk copy)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(unsigned long long* mb, unsigned count) {
@@ -879,6 +880,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* mb, unsign
   for (int i = 0; i < (1 << 22); ++i)
     if (mbar_try_wait(mb, parity)) return true;
   return false;
+}
+// contiguous copy of `bytes` (a multiple of 16; both addresses 16-byte
+// aligned) into shared memory, completion counted on mb
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* mb) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(mb))
+      : "memory");
 }
 // 2-D tile load: box at element coordinates (x, y) of the tensor map into
 // shared memory at dst (128-byte aligned), completion counted on mb
@@ -999,12 +1009,19 @@ __device__ __forceinline__ void issue_unit(const PassArgs<typename K::real>& A, 
   }
 }
 
-// float32 column passes may stage their tiles with TMA: the tile of S
-// columns (S x 8 bytes, a multiple of 16) and NS rows is dense in shared
-// memory in the order the cp.async path writes it
+// float32 passes may stage their tiles with TMA where the tile lies in
+// shared memory exactly as in global memory up to a 2-D box: a column tile
+// (S columns of S x 8 bytes, a multiple of 16, by NS rows, dense) or an
+// unswizzled slot-major tile of contiguous transforms or rows (single pass,
+// or the row pass of a two-pass plan, whose S rows are adjacent)
 template <class K> constexpr bool tma_ok() {
-  return K::KIND == KIND_COL && std::is_same<typename K::real, float>::value && (K::S * 8) % 16 == 0 &&
-         K::S <= 256 && (stage_bytes<K>() % 128) == 0;
+  if constexpr (!std::is_same<typename K::real, float>::value || (stage_bytes<K>() % 128) != 0) {
+    return false;
+  } else if constexpr (K::KIND == KIND_COL) {
+    return (K::S * 8) % 16 == 0 && K::S <= 256;
+  } else {
+    return !StageSwz<K>::ON && !StageSwz<K>::PAIRS && !K::SLOT_FAST && (K::NS * 8) % 16 == 0;
+  }
 }
 template <class K> constexpr int tma_box_rows() { return K::NS < 256 ? K::NS : 256; }
 // Issue the TMA copies of column-pass unit `unit`'s tile (one thread): the
@@ -1014,17 +1031,41 @@ template <class K> constexpr int tma_box_rows() { return K::NS < 256 ? K::NS : 2
 template <class K>
 __device__ __forceinline__ void issue_unit_tma(const PassArgs<typename K::real>& A, const CUtensorMap* tm,
                                                long long unit, char* stage, unsigned long long* mb) {
-  long long b;
-  int c0;
-  col_unit<K>(A.geo, unit, b, c0);
-  constexpr int BR = tma_box_rows<K>();
-  constexpr unsigned bytes = (unsigned)(K::NS * K::S * sizeof(typename K::c));
-  const int row0 = (int)(b * (A.geo.n / A.geo.n2));
-  fence_proxy_async_smem();
-  mbar_arrive_expect_tx(mb, bytes);
+  using c = typename K::c;
+  const Geo& g = A.geo;
+  if constexpr (K::KIND == KIND_COL) {
+    long long b;
+    int c0;
+    col_unit<K>(g, unit, b, c0);
+    constexpr int BR = tma_box_rows<K>();
+    constexpr unsigned bytes = (unsigned)(K::NS * K::S * sizeof(c));
+    const int row0 = (int)(b * (g.n / g.n2));
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(mb, bytes);
 #pragma unroll
-  for (int r = 0; r < K::NS / BR; ++r)
-    tma_load_2d(stage + (size_t)r * BR * K::S * sizeof(typename K::c), tm, c0, row0 + r * BR, mb);
+    for (int r = 0; r < K::NS / BR; ++r) tma_load_2d(stage + (size_t)r * BR * K::S * sizeof(c), tm, c0, row0 + r * BR, mb);
+  } else {
+    // the tile is contiguous in global memory: the nv valid transforms of a
+    // single-pass unit (a ragged last unit copies only those), or the S
+    // adjacent rows r0 .. r0 + S - 1 of transform b of a row pass
+    const c* src;
+    long long nv = K::S;
+    if constexpr (K::KIND == KIND_SP) {
+      const long long first = unit * K::S;
+      nv = g.batch - first;
+      if (nv > K::S) nv = K::S;
+      src = A.in + first * K::NS;
+    } else {
+      const int blocks = g.n1 / K::S;
+      const long long b = unit / blocks;
+      const int r0 = (int)(unit - b * blocks) * K::S;
+      src = A.in + b * g.n + (long long)r0 * g.n2;
+    }
+    const unsigned bytes = (unsigned)(nv * K::NS * (long long)sizeof(c));
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(mb, bytes);
+    bulk_load(stage, src, bytes, mb);
+  }
 }
 
 __device__ __forceinline__ void atomic_max_nonneg(float* addr, float v) {
@@ -1127,7 +1168,7 @@ __device__ __forceinline__ void pass_body(const PassArgs<typename K::real>& A, c
     for (int i = 0; i < E; ++i) { xs[i] = mk<c>(0, 0); ys[i] = mk<c>(0, 0); }
   }
 
-  static_assert(!TMA || tma_ok<K>(), "TMA staging: float32 column passes");
+  static_assert(!TMA || tma_ok<K>(), "TMA staging: float32 passes with an unswizzled tile");
   __shared__ __align__(8) unsigned long long tma_mb[TMA ? NSTAGE : 1];
   __shared__ int tma_fail;
   if constexpr (TMA) {
@@ -1671,8 +1712,9 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
   }
 }
 
-// The pass kernel with TMA-staged tiles (float32 column passes).  The tensor
-// map is a kernel parameter (__grid_constant__: TMA reads it in place).  The
+// The pass kernel with TMA-staged tiles (float32).  The tensor map of a
+// column pass is a kernel parameter (__grid_constant__: TMA reads it in
+// place); single and row passes copy contiguous tiles and ignore it.  The
 // launch adds 128 bytes of dynamic shared memory so that the ring can start
 // on a 128-byte boundary, as TMA destinations must.
 template <class K> constexpr int tma_smem_bytes(int ftm) {

@@ -69,7 +69,25 @@ bool set_smem_attrs(const KernelEntry* ke) {
   return true;
 }
 
-std::atomic<int> g_column_tma{1};
+std::atomic<int> g_tma_staging{1};
+
+// TMA staging where it measured faster than cp.async on one GB300 (float32,
+// 2^28 elements per call, forward, with and without checksums):
+//  - row passes (one bulk copy of S adjacent rows): 1-4% faster at every
+//    measured N1 x N2 (2^16 .. 2^21);
+//  - column passes: tile rows of 64 bytes or more, at N1 >= 512 or with
+//    checksums on (N1 = 128, 256 without checksums ran 2-5% slower; tile
+//    rows of 16-32 bytes 1-24% slower);
+//  - single passes: where it won by more than the run-to-run spread, N =
+//    4096 (+9% / +5% without / with checksums), 1024 and 2048 with checksums
+//    (+6%, +3%), 256 and 8192 without (+3%, +5%); the other cases ran 1-5%
+//    slower and stay on cp.async.
+bool tma_faster(const KernelEntry* ke, int ft_mode) {
+  const bool ft = ft_mode != TURBOFFT_FT_OFF;
+  if (ke->kind == tf::KIND_ROW) return true;
+  if (ke->kind == tf::KIND_COL) return ke->s * 8 >= 64 && (ke->ns >= 512 || ft);
+  return ke->ns == 4096 || (ft ? (ke->ns == 1024 || ke->ns == 2048) : (ke->ns == 256 || ke->ns == 8192));
+}
 
 namespace {
 // the driver's tensor-map encoder, looked up once through the runtime
@@ -332,10 +350,13 @@ turbofft_status run(turbofft_plan* p, const void* in, void* out, void* scratch, 
       tf::PassArgs<float> A;
       fill_args<float>(p, pi, pin, pout, batch, tbase, inj, A);
       const int v = ft_variant(p->ft_mode);
-      // the column pass of a two-pass plan: tiles staged by TMA where it can
+      // tiles staged by TMA where the plan chose it and the exec's input
+      // allows it (a column pass: a tensor map of the input; others copy
+      // contiguous tiles and ignore the map)
       CUtensorMap tm;
-      const bool tma = pi == 0 && p->tma && p->num_passes == 2 && p->d_tab == nullptr && v <= 1 &&
-                       pp.ke->main_tma[v] && encode_column_map(p, pin, batch, &tm);
+      memset(&tm, 0, sizeof(tm));
+      const bool tma = ((p->tma_mask >> pi) & 1) && p->num_passes <= 2 && p->d_tab == nullptr && v <= 1 &&
+                       pp.ke->main_tma[v] && (pp.kind != tf::KIND_COL || encode_column_map(p, pin, batch, &tm));
       timed(2 * pi, [&] {
         if (tma)
           pp.ke->main_tma[v](&A, &tm, grid, stream);

@@ -160,10 +160,11 @@ struct turbofft_plan {
   // float64 two-pass plan with checksums over whole transforms (column pass
   // v.x, row pass e.y, check and recompute kernels after the row pass)
   bool tchk = false;
-  // float32 two-pass plan: the column pass stages its tiles with TMA copies
-  // where the exec's input allows it (encode_column_map); d_err receives the
-  // kernel's timeout flag (the FtState's error field with checksums on)
-  bool tma = false;
+  // float32 one- and two-pass plans: bit pi set if pass pi stages its tiles
+  // with TMA copies (a column pass where encode_column_map can describe the
+  // exec's input); d_err receives the kernels' timeout flag (the FtState's
+  // error field with checksums on)
+  int tma_mask = 0;
   int* d_err = nullptr;
   void* d_vcol = nullptr;
   void* d_erow = nullptr;
@@ -278,7 +279,8 @@ double time_with_temp(turbofft_plan* p);
 void drop_graph(turbofft_plan* p);
 turbofft_status exec_ragged(turbofft_plan* p, const void* in, void* out, cudaStream_t s);
 extern std::atomic<int> g_ragged_single;  // new ragged plans use the persistent kernel where they can
-extern std::atomic<int> g_column_tma;     // new float32 two-pass plans stage column tiles with TMA
+extern std::atomic<int> g_tma_staging;    // TMA staging of new float32 plans: 0 never, 1 where faster, 2 always
+bool tma_faster(const KernelEntry* ke, int ft_mode);  // mode 1's rule (tf_launch.cu)
 void rg_free(turbofft_plan* p);
 bool rg_timed_out(const turbofft_plan* p);  // the last exec's grid barrier gave up waiting
 

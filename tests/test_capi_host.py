@@ -188,13 +188,13 @@ def test_thread_level_mode_rejected_where_it_cannot_apply(L):
 def test_process_wide_switches_need_no_device(L):
     """The staging / launch-form switches only record a choice for plans
     created afterwards."""
-    for f in (L.turbofft_set_column_tma, L.turbofft_set_ragged_single_launch):
+    for f in (L.turbofft_set_tma_staging, L.turbofft_set_ragged_single_launch):
         assert f(0) == tfl.SUCCESS
         assert f(1) == tfl.SUCCESS
-    assert L.turbofft_set_column_tma(2) == tfl.SUCCESS
-    assert L.turbofft_set_column_tma(3) == tfl.INVALID_VALUE
-    assert L.turbofft_set_column_tma(-1) == tfl.INVALID_VALUE
-    assert L.turbofft_set_column_tma(1) == tfl.SUCCESS
+    assert L.turbofft_set_tma_staging(2) == tfl.SUCCESS
+    assert L.turbofft_set_tma_staging(3) == tfl.INVALID_VALUE
+    assert L.turbofft_set_tma_staging(-1) == tfl.INVALID_VALUE
+    assert L.turbofft_set_tma_staging(1) == tfl.SUCCESS
 
 
 def test_plan_info_layout_matches_header():
