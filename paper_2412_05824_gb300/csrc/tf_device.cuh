@@ -226,8 +226,13 @@ template <typename C> struct Dft<C, 2> {
 __device__ __forceinline__ void lf_bfly(double2& a, double2& b, double2 w) {
   const bool sw = (__double2loint(w.y) & 1) != 0;
   const double t = w.y, cc = w.x;
-  // b' = b, or i b = (-b.im, b.re) (sign by integer xor, off the FP64 pipe)
-  const double nbi = __longlong_as_double(__double_as_longlong(b.y) ^ (long long)0x8000000000000000ull);
+  // b' = b, or i b = (-b.im, b.re).  The sign is flipped by an integer xor
+  // of the high word in inline PTX: written as a plain C++ bit operation
+  // the compiler recognises a negation and may emit it as a float64
+  // instruction, which on GB300 costs a slot of the FP64 pipe
+  int nbi_hi = __double2hiint(b.y);
+  asm("xor.b32 %0, %0, 0x80000000;" : "+r"(nbi_hi));
+  const double nbi = __hiloint2double(nbi_hi, __double2loint(b.y));
   const double pr = sw ? nbi : b.x;
   const double pi = sw ? b.x : b.y;
   const double u = fma(-t, pi, pr);
