@@ -550,6 +550,12 @@ struct Geo {
   // column tables), 0 = the columns of one transform first (transform-level
   // checksums accumulate per transform)
   int col_tfast;
+  // log2 of n1, n2 and outer (all powers of two): the column and row passes
+  // split unit and signal indices with shifts and masks.  A 64-bit integer
+  // division is a library sequence whose rarely taken branches still issue
+  // float64 instructions (predicated off) on the FP64 pipe, the pipe that
+  // bounds the float64 kernels.
+  int l2n1, l2n2, l2outer;
 };
 
 __device__ __forceinline__ long long tr_base(const long long* tab, long long b, long long n) {
@@ -559,10 +565,10 @@ __device__ __forceinline__ long long tr_base(const long long* tab, long long b, 
 // three-pass last pass: first sub-transform of unit `unit` (units walk
 // transform t, then row k2, then blocks of S adjacent sub-transforms)
 template <class K> __device__ __forceinline__ long long row_unit_first(const Geo& g, long long unit) {
-  const int kblocks = g.outer / K::S;
-  const long long per_t = (long long)g.n1 * kblocks;
-  const long long t = unit / per_t;
-  const int kb = (int)((unit - t * per_t) % kblocks);
+  // per transform n1 * (outer / S) units; kb = unit mod (outer / S)
+  constexpr int LS = ILog2<K::S>::v;
+  const long long t = unit >> (g.l2n1 + g.l2outer - LS);
+  const int kb = (int)(unit & ((1ll << (g.l2outer - LS)) - 1));
   return t * g.outer + (long long)kb * K::S;
 }
 
@@ -574,13 +580,15 @@ template <class K> __device__ __forceinline__ long long row_unit_first(const Geo
 template <class K>
 __device__ __forceinline__ void col_unit(const Geo& g, long long unit, long long& b, int& c0) {
   if (std::is_same<typename K::real, double>::value && g.col_tfast) {
-    const long long cb = unit / g.batch;
-    b = unit - cb * g.batch;
+    // (unit indices stay below 2^32: a 32-bit division)
+    const unsigned u = (unsigned)unit, bt = (unsigned)g.batch;
+    const unsigned cb = u / bt;
+    b = (long long)(u - cb * bt);
     c0 = (int)cb * K::S;
   } else {
-    const int blocks = g.n2 / K::S;
-    b = unit / blocks;
-    c0 = (int)(unit - b * blocks) * K::S;
+    constexpr int LS = ILog2<K::S>::v;
+    b = unit >> (g.l2n2 - LS);
+    c0 = (int)(unit & ((1ll << (g.l2n2 - LS)) - 1)) * K::S;
   }
 }
 
@@ -599,14 +607,14 @@ template <class K> __device__ __forceinline__ long long signal_of(const Geo& g, 
       // last pass of a three-pass plan: the S rows of a unit are row k2 of
       // S adjacent sub-transforms (adjacent first-pass outputs k1), whose
       // results are adjacent in the final output
+      constexpr int LS = ILog2<K::S>::v;
       const long long b0 = row_unit_first<K>(g, unit);
-      const long long per_t = (long long)g.n1 * (g.outer / K::S);
-      const int k2 = (int)((unit % per_t) / (g.outer / K::S));
+      const int k2 = (int)((unit >> (g.l2outer - LS)) & (g.n1 - 1));
       return (b0 + slot) * g.n1 + k2;
     }
-    const int blocks = g.n1 / K::S;
-    long long b = unit / blocks;
-    int k1 = (int)(unit - b * blocks) * K::S + slot;
+    constexpr int LS = ILog2<K::S>::v;
+    const long long b = unit >> (g.l2n1 - LS);
+    const int k1 = (int)(unit & ((1ll << (g.l2n1 - LS)) - 1)) * K::S + slot;
     return b * g.n1 + k1;
   }
 }
@@ -620,11 +628,9 @@ template <class K> __device__ __forceinline__ long long in_base(const Geo& g, lo
   if constexpr (K::KIND == KIND_SP) {
     return tr_base(g.in_tab, sig, g.n);
   } else if constexpr (K::KIND == KIND_COL) {
-    const long long b = sig / g.n2;
-    return tr_base(g.in_tab, b, g.n) + (sig - b * g.n2);
+    return tr_base(g.in_tab, sig >> g.l2n2, g.n) + (sig & (g.n2 - 1));
   } else {
-    const long long b = sig / g.n1;
-    return tr_base(g.in_tab, b, g.n) + (sig - b * g.n1) * g.n2;
+    return tr_base(g.in_tab, sig >> g.l2n1, g.n) + (sig & (g.n1 - 1)) * g.n2;
   }
 }
 template <class K> __device__ __forceinline__ long long in_step(const Geo& g) {
@@ -634,15 +640,13 @@ template <class K> __device__ __forceinline__ long long out_base(const Geo& g, l
   if constexpr (K::KIND == KIND_SP) {
     return tr_base(g.out_tab, sig, g.n);
   } else if constexpr (K::KIND == KIND_COL) {
-    const long long b = sig / g.n2;
-    return tr_base(g.out_tab, b, g.n) + (sig - b * g.n2);
+    return tr_base(g.out_tab, sig >> g.l2n2, g.n) + (sig & (g.n2 - 1));
   } else {
-    const long long b = sig / g.n1;
+    const long long b = sig >> g.l2n1;
     if (g.outer > 1) {
-      const long long tb = b / g.outer;
-      return tr_base(g.out_tab, tb, g.n_outer) + (b - tb * g.outer) + (sig - b * g.n1) * g.outer;
+      return tr_base(g.out_tab, b >> g.l2outer, g.n_outer) + (b & (g.outer - 1)) + (sig & (g.n1 - 1)) * g.outer;
     }
-    return tr_base(g.out_tab, b, g.n) + (sig - b * g.n1);
+    return tr_base(g.out_tab, b, g.n) + (sig & (g.n1 - 1));
   }
 }
 template <class K> __device__ __forceinline__ long long out_step(const Geo& g) {
@@ -662,8 +666,7 @@ template <class K> __device__ __forceinline__ long long out_off(const Geo& g, lo
 template <class K> __device__ __forceinline__ typename K::c colTwiddle(const Geo& g, const typename K::c* tlo,
                                                                        const typename K::c* thi, long long sig,
                                                                        int k1) {
-  long long b = sig / g.n2;
-  int n2 = (int)(sig - b * g.n2);
+  const int n2 = (int)(sig & (g.n2 - 1));
   unsigned q = (unsigned)k1 * (unsigned)n2;
   return cmul(ldg(thi + (q >> 12)), ldg(tlo + (q & 4095u)));
 }
@@ -713,7 +716,7 @@ template <typename R> struct PassArgs {
 
 // column n2 of a column-pass signal (within its transform)
 template <class K> __device__ __forceinline__ long long col_of(const Geo& g, long long sig) {
-  return sig - (sig / g.n2) * g.n2;
+  return sig & (g.n2 - 1);
 }
 // inter-pass twiddle of a column pass: from the float64 table in access
 // order, else the product of the two small tables
@@ -977,9 +980,9 @@ __device__ __forceinline__ void issue_unit(const PassArgs<typename K::real>& A, 
     if (g.outer > 1) {
       // rows of S different sub-transforms: one contiguous run per slot
       constexpr int cps = K::NS * (int)sizeof(c) / 16;
+      constexpr int LS = ILog2<K::S>::v;
       const long long b0 = row_unit_first<K>(g, unit);
-      const long long per_t = (long long)g.n1 * (g.outer / K::S);
-      const int k2 = (int)((unit % per_t) / (g.outer / K::S));
+      const int k2 = (int)((unit >> (g.l2outer - LS)) & (g.n1 - 1));
       const c* base = A.in + b0 * g.n + (long long)k2 * g.n2;
       for (int q = tid; q < K::S * cps; q += K::NT) {
         const int sl = q / cps, j = q - sl * cps;
@@ -988,9 +991,9 @@ __device__ __forceinline__ void issue_unit(const PassArgs<typename K::real>& A, 
       }
       return;
     }
-    const int blocks = g.n1 / K::S;
-    const long long b = unit / blocks;
-    const int r0 = (int)(unit - b * blocks) * K::S;
+    constexpr int LS = ILog2<K::S>::v;
+    const long long b = unit >> (g.l2n1 - LS);
+    const int r0 = (int)(unit & ((1ll << (g.l2n1 - LS)) - 1)) * K::S;
     const char* src = reinterpret_cast<const char*>(A.in + tr_base(g.in_tab, b, g.n) + (long long)r0 * g.n2);
     constexpr int cps = K::NS * (int)sizeof(c) / 16;
     constexpr int chunks = K::S * cps;
@@ -1044,7 +1047,7 @@ __device__ __forceinline__ void issue_unit_tma(const PassArgs<typename K::real>&
     col_unit<K>(g, unit, b, c0);
     constexpr int BR = tma_box_rows<K>();
     constexpr unsigned bytes = (unsigned)(K::NS * K::S * sizeof(c));
-    const int row0 = (int)(b * (g.n / g.n2));
+    const int row0 = (int)(b << g.l2n1);  // b * (n / n2) = b * n1
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(mb, bytes);
 #pragma unroll
@@ -1061,9 +1064,9 @@ __device__ __forceinline__ void issue_unit_tma(const PassArgs<typename K::real>&
       if (nv > K::S) nv = K::S;
       src = A.in + first * K::NS;
     } else {
-      const int blocks = g.n1 / K::S;
-      const long long b = unit / blocks;
-      const int r0 = (int)(unit - b * blocks) * K::S;
+      constexpr int LS = ILog2<K::S>::v;
+      const long long b = unit >> (g.l2n1 - LS);
+      const int r0 = (int)(unit & ((1ll << (g.l2n1 - LS)) - 1)) * K::S;
       src = A.in + b * g.n + (long long)r0 * g.n2;
     }
     const unsigned bytes = (unsigned)(nv * K::NS * (long long)sizeof(c));
@@ -1085,7 +1088,7 @@ template <class K> __device__ __forceinline__ void block_sum3(double* red, doubl
 // transform of work unit `unit` of a column / row pass
 template <class K> __device__ __forceinline__ long long unit_transform(const Geo& g, long long unit) {
   const long long sig = signal_of<K>(g, unit, 0);
-  return K::KIND == KIND_COL ? sig / g.n2 : sig / g.n1;
+  return K::KIND == KIND_COL ? sig >> g.l2n2 : sig >> g.l2n1;
 }
 
 // FTM: 0 = no checksums; 1 = checksums, right-side sums formed on the rare
@@ -1365,7 +1368,7 @@ __device__ __forceinline__ void pass_body(const PassArgs<typename K::real>& A, c
           if constexpr (EAGER) ys[i] = cadd(ys[i], a[i]);
           if constexpr (TC) {
             // e.y with the N-point weights of row k1 (contiguous)
-            const long long k1 = valid ? sig - (sig / g.n1) * g.n1 : 0;
+            const long long k1 = valid ? (sig & (g.n1 - 1)) : 0;
             cmac(pout, ldg(A.erow + k1 * K::NS + pos), a[i]);
           } else if constexpr (FT) {
             cmac(pout, weight<K>(evp, pos), a[i]);
@@ -1701,7 +1704,9 @@ __global__ void __launch_bounds__(K::NT, FTM ? TwMode<K, TF_FT_TW_BUDGET>::MINB_
       if (parts < 1) parts = 1;
       const long long items = batch * parts;
       for (long long i = blockIdx.x; i < items; i += gridDim.x) {
-        const long long b = i % batch, part = i / batch;
+        // (item indices stay below 2^32: a 32-bit division)
+        const unsigned ui = (unsigned)i, ub32 = (unsigned)batch;
+        const long long part = ui / ub32, b = ui - (unsigned)part * ub32;
         __syncthreads();
         pass_body<K, FTM>(A, reinterpret_cast<char*>(smem_raw_), b * ub + part, parts, (b + 1) * ub);
       }

@@ -213,6 +213,9 @@ void fill_args(const turbofft_plan* p, int pi, const void* in, void* out, int64_
   A.geo.out_tab = (pi == p->num_passes - 1) ? p->d_tab : nullptr;
   A.geo.outer = pp.outer;
   A.geo.n_outer = p->n;
+  A.geo.l2n1 = ilog2_exact(pp.g_n1);
+  A.geo.l2n2 = ilog2_exact(pp.g_n2);
+  A.geo.l2outer = pp.outer > 1 ? ilog2_exact(pp.outer) : 0;
   A.num_units = p->cl ? batch : units_for(p, pi, batch);  // cluster plans: one unit per transform
   const bool inverse = p->direction > 0;
   const bool scaled = p->direction == TURBOFFT_INVERSE || p->direction == TURBOFFT_FORWARD_SCALED;
