@@ -1266,7 +1266,9 @@ __device__ __forceinline__ void pass_body(const PassArgs<typename K::real>& A, c
         enf = fmaf(fy, fy, enf);
       }
       double et = enf;
-      if (!isfinite(enf)) {
+      // (a warp-uniform condition: the compiler branches around this rare
+      // float64 code instead of issuing it predicated off on every pass)
+      if (__any_sync(0xffffffffu, !isfinite(enf))) {
         et = 0;
 #pragma unroll
         for (int i = 0; i < E; ++i) et = fma(a[i].x, a[i].x, fma(a[i].y, a[i].y, et));
@@ -1301,7 +1303,9 @@ __device__ __forceinline__ void pass_body(const PassArgs<typename K::real>& A, c
           enf = fmaf(fx, fx, enf);
           enf = fmaf(fy, fy, enf);
         }
-        if (isfinite(enf)) {
+        // (a warp-uniform condition: the compiler branches around the rare
+        // float64 code instead of issuing it predicated off on every pass)
+        if (!__any_sync(0xffffffffu, !isfinite(enf))) {
           en += (R)enf;
         } else {
           // values beyond the float32 range: the exact energy (rare)
@@ -1429,8 +1433,10 @@ __device__ __forceinline__ void pass_body(const PassArgs<typename K::real>& A, c
         }
       }
     }
-    // ---- store (scaled inverse: one uniform branch around the scaling)
-    if (scaled) {
+    // ---- store (scaled inverse: one uniform branch around the scaling; a
+    // column pass is never last and has no scaling code, which would
+    // otherwise be issued as predicated-off multiplies)
+    if (K::KIND != KIND_COL && scaled) {
       if constexpr (std::is_same<R, double>::value && K::KIND != KIND_COL) {  // (a column pass is never last)
         // the scale 2^-k only lowers exponents: where every value of the
         // warp is zero or keeps a normal result, subtract k from the
