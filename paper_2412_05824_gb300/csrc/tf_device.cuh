@@ -92,9 +92,9 @@ __device__ __forceinline__ cdd conj_mask(cdd v, unsigned long long m) {
 // that only scales the checksum threshold.  Exponents below the float range
 // give 0 or a subnormal, above it the float exponent 254 (the caller checks
 // the sum for overflow and falls back to float64).
-__device__ __forceinline__ float abs_as_float(double v) {
+__device__ __forceinline__ float abs_as_float(double v, int down = 0) {
   const int hi = __double2hiint(v);
-  int fe = ((hi >> 20) & 0x7FF) - 1023 + 127;
+  int fe = ((hi >> 20) & 0x7FF) - 1023 + 127 - down;
   fe = fe < 0 ? 0 : (fe > 254 ? 254 : fe);
   return __uint_as_float(((unsigned)fe << 23) | (((unsigned)hi & 0xFFFFFu) << 3));
 }
@@ -1257,22 +1257,22 @@ __device__ __forceinline__ void pass_body(const PassArgs<typename K::real>& A, c
       // v.x with the N-point weights in access order, and the energy (in
       // float32 from integer-extracted bits, as below)
       const long long vb = col_of<K>(g, valid ? sig : 0) * K::NS;
-      float enf = 0.f;
+      // the energy twice, of x and of x 2^-64, so that values beyond the
+      // float32 range (to about 2^125) need no float64 fallback: float64
+      // code under a condition would be issued, predicated off, on every
+      // pass
+      float enf = 0.f, enl = 0.f;
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         cmac(pin, ldg(A.vcol + vb + t + i * P), a[i]);
         const float fx = abs_as_float(a[i].x), fy = abs_as_float(a[i].y);
         enf = fmaf(fx, fx, enf);
         enf = fmaf(fy, fy, enf);
+        const float lx = abs_as_float(a[i].x, 64), ly = abs_as_float(a[i].y, 64);
+        enl = fmaf(lx, lx, enl);
+        enl = fmaf(ly, ly, enl);
       }
-      double et = enf;
-      // (a warp-uniform condition: the compiler branches around this rare
-      // float64 code instead of issuing it predicated off on every pass)
-      if (__any_sync(0xffffffffu, !isfinite(enf))) {
-        et = 0;
-#pragma unroll
-        for (int i = 0; i < E; ++i) et = fma(a[i].x, a[i].x, fma(a[i].y, a[i].y, et));
-      }
+      const double et = isfinite(enf) ? (double)enf : (double)enl * 0x1p128;
       tc0 += pin.x;
       tc1 += pin.y;
       tc2 += et;
@@ -1294,7 +1294,10 @@ __device__ __forceinline__ void pass_body(const PassArgs<typename K::real>& A, c
         // float64: the energy only scales tau, so it is accumulated in
         // float32 from converted values, keeping the float64 pipe for the
         // transform and the checksum products
-        float enf = 0.f;
+        // (twice, of x and of x 2^-64, so that values beyond the float32
+        // range, to about 2^125, need no float64 fallback: float64 code
+        // under a condition would be issued, predicated off, on every pass)
+        float enf = 0.f, enl = 0.f;
 #pragma unroll
         for (int i = 0; i < E; ++i) {
           if constexpr (EAGER) xs[i] = cadd(xs[i], a[i]);
@@ -1302,19 +1305,11 @@ __device__ __forceinline__ void pass_body(const PassArgs<typename K::real>& A, c
           const float fx = abs_as_float(a[i].x), fy = abs_as_float(a[i].y);
           enf = fmaf(fx, fx, enf);
           enf = fmaf(fy, fy, enf);
+          const float lx = abs_as_float(a[i].x, 64), ly = abs_as_float(a[i].y, 64);
+          enl = fmaf(lx, lx, enl);
+          enl = fmaf(ly, ly, enl);
         }
-        // (a warp-uniform condition: the compiler branches around the rare
-        // float64 code instead of issuing it predicated off on every pass)
-        if (!__any_sync(0xffffffffu, !isfinite(enf))) {
-          en += (R)enf;
-        } else {
-          // values beyond the float32 range: the exact energy (rare)
-#pragma unroll
-          for (int i = 0; i < E; ++i) {
-            en = fma(a[i].x, a[i].x, en);
-            en = fma(a[i].y, a[i].y, en);
-          }
-        }
+        en += isfinite(enf) ? (R)enf : (R)enl * (R)0x1p128;
       } else {
         if constexpr (std::is_same<R, float>::value) {
           // energy (re^2, im^2) as one paired FP32 FMA per value

@@ -302,3 +302,28 @@ def test_float64_whole_transform_checks_other_directions(direction):
             assert rep["corrected"] == 1 and rep["first_transform"] == 4
         assert float(np.max(oracle.rel_l2(y, ref))) <= tol
     plan.close()
+
+
+@pytest.mark.parametrize("n,batch", [(1024, 40), (1 << 16, 3)])
+@pytest.mark.parametrize("scale_log2", [70, 110])
+def test_float64_checks_beyond_the_float32_range(n, batch, scale_log2):
+    """float64 data far beyond the float32 range (|x| ~ 2^70 and 2^110, so
+    that the threshold's energy sum overflows float32): no false alarm, and
+    an exponent flip is detected and corrected (single pass: block-level
+    checks; 2^16: whole-transform checks)."""
+    x = ss.uniform_complex(31, batch, n, np.float64) * 2.0 ** scale_log2
+    xd = torch.from_numpy(x).cuda()
+    ref = oracle.fft(x)
+    tol = oracle.tolerance(np.float64, n)
+    p = tfl.Plan(n, batch, "complex128", "forward", "correct")
+    y = p.exec(xd).cpu().numpy()
+    rep = p.report()
+    assert rep["detected"] == 0 and rep["status"] == tfl.SUCCESS, rep
+    assert float(np.max(oracle.rel_l2(y, ref))) <= tol
+    p.inject(batch // 2, 0, 1, 77, 0, 61)
+    y = p.exec(xd).cpu().numpy()
+    rep = p.report()
+    assert rep["detected"] >= 1 and rep["corrected"] >= 1 and rep["status"] == tfl.SUCCESS, rep
+    assert rep["first_transform"] == batch // 2, rep
+    assert float(np.max(oracle.rel_l2(y, ref))) <= tol
+    p.close()
