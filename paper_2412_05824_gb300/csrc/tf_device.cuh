@@ -87,11 +87,11 @@ __device__ __forceinline__ cdd conj_mask(cdd v, unsigned long long m) {
   const unsigned f = m ? 0x80000000u : 0u;
   return cdd{v.x, dd(__uint_as_float(__float_as_uint(v.y.hi) ^ f), __uint_as_float(__float_as_uint(v.y.lo) ^ f))};
 }
-// |v| of a double as a float built with integer operations from its
+// |v| 2^-down of a double as a float built with integer operations from its
 // exponent and top 20 mantissa bits (relative error < 2^-20): for the energy
 // that only scales the checksum threshold.  Exponents below the float range
-// give 0 or a subnormal, above it the float exponent 254 (the caller checks
-// the sum for overflow and falls back to float64).
+// give 0 or a subnormal, above it the float exponent 254 (the callers keep a
+// second sum with down = 64 for sums that overflow).
 __device__ __forceinline__ float abs_as_float(double v, int down = 0) {
   const int hi = __double2hiint(v);
   int fe = ((hi >> 20) & 0x7FF) - 1023 + 127 - down;
